@@ -1,0 +1,322 @@
+"""Throughput of the batched multigrid HF-QMC sweep on one GB300.
+
+Workload (default "multigrid_L100_240"): Bethe lattice (W = 4) at half
+filling, U = 5, beta = 40, six dtau grids Lambda in {100,120,140,160,200,240},
+64 independent chains per grid, all 384 chains in one persistent launch,
+FP32 G with delayed rank-k updates (split-TF32 tensor-core flush) and periodic
+FP64 recomputation.  One step = one hfqmc_sweep call of --sweeps measured
+sweeps on every chain (1000 by default; the paper-shaped run is 10^3 warm-up
++ 10^4 measured sweeps = 11 such steps).  The metric is HS flip proposals per
+second: sum over chains of Lambda x sweeps, divided by device time.
+
+Printed (one JSON line, rank 0): value (device-timed, inputs resident),
+e2e (same metric through the C ABI from pinned host buffers, G0 upload and
+G(tau) download in the timed region), roofline of the sweep kernel,
+cpu_baseline (the FP64 oracle on the host cores, bounded sample), the FP64
+rank-1 GPU path on the same workload, and the FP32-vs-FP64 G(tau) error.
+
+--impl reference runs the oracle (the plain FP64 CPU HF-QMC) on the same
+workload shape as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="multigrid_L100_240")
+    ap.add_argument("--sweeps", type=int, default=1000, help="measured sweeps per step")
+    ap.add_argument("--precision", default="f32_delayed")
+    ap.add_argument("--flush", default="auto")
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--n-wrap", type=int, default=0)
+    ap.add_argument("--no-baselines", action="store_true", help="skip the oracle / FP64 legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--chains", type=int, default=0, help="override chains per grid (small cases)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    from paper_0801_1222_gb300 import inputs
+    w = inputs.WORKLOADS[name]
+    grids = inputs.workload_grids(name)
+    return w, grids
+
+
+def proposals_per_sweep(grids):
+    return sum(L * c for (_, _, L, c) in grids)
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# -------------------------------------------------------------------------
+# reference arm / cpu baseline: the FP64 oracle on the host cores
+# -------------------------------------------------------------------------
+def oracle_sample(grids, beta, seconds, sweeps_hint=None):
+    """Times the oracle on a bounded sample of the workload: every grid gets
+    chains in proportion to the workload, n_cores chains in total, and the
+    sweep count is grown until the sample takes about `seconds`."""
+    import oracle
+    from paper_0801_1222_gb300 import inputs
+    cores = os.cpu_count() or 1
+    per = max(1, cores // len(grids))
+    q = oracle.OracleHFQMC(beta, [(U, dt) for (U, dt, L, c) in grids], [per] * len(grids), seed=1,
+                           n_wrap=4096, threads=cores)
+    for i, (U, dt, L, c) in enumerate(grids):
+        q.set_G0(i, inputs.bethe_G0_tau(beta, L))
+    sweeps = sweeps_hint or 2
+    t0 = time.perf_counter()
+    q.sweep(0, sweeps)
+    dt_ = time.perf_counter() - t0
+    if sweeps_hint is None:
+        sweeps = max(2, int(sweeps * (seconds / max(dt_, 1e-3))))
+        t0 = time.perf_counter()
+        q.sweep(0, sweeps)
+        dt_ = time.perf_counter() - t0
+    props = sweeps * sum(L * per for (_, _, L, _) in grids)
+    return {"value": props / dt_, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{per} chain(s) x {len(grids)} grids x {sweeps} sweeps (FP64 rank-1, "
+                      f"n_wrap 4096), {dt_:.1f} s on {cores} host threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w, grids = workload(args.workload)
+    beta = w["beta"]
+    for _ in range(args.warmup):
+        oracle_sample(grids, beta, 0, sweeps_hint=1)
+    times, props = [], 0
+    cb = None
+    for _ in range(args.steps):
+        r = oracle_sample(grids, beta, min(args.cpu_seconds, 60.0) / max(args.steps, 1))
+        times.append(1.0 / r["value"])
+        cb = r
+    value = statistics.median([1.0 / t for t in times])
+    line = {"impl": "reference", "metric": "HS flip proposals/s", "value": value,
+            "unit": "proposals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "beta": beta,
+                                            "grids_L": [g[2] for g in grids]},
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": "proposals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------------
+# our arm
+# -------------------------------------------------------------------------
+def make_ctx(hfqmc, inputs, beta, grids, precision, args, stream, seed=1):
+    U = [g[0] for g in grids]
+    dtau = [g[1] for g in grids]
+    chains = [g[3] for g in grids]
+    ctx = hfqmc.HFQMC(beta, U, dtau, chains, seed=seed, precision=precision, k=args.k,
+                      n_wrap=args.n_wrap, flush=args.flush, drift_fail=1.0, stream=stream)
+    g0 = [inputs.bethe_G0_tau(beta, g[2]) for g in grids]
+    for i in range(len(grids)):
+        ctx.set_G0(i, g0[i])
+    return ctx, g0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_0801_1222_gb300 import hfqmc, inputs
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w, grids = workload(args.workload)
+    if args.chains:
+        grids = [(U, dt, L, args.chains) for (U, dt, L, _) in grids]
+    beta = w["beta"]
+    stream = torch.cuda.Stream()
+    pps = proposals_per_sweep(grids)
+    S = args.sweeps
+    ctx, g0 = make_ctx(hfqmc, inputs, beta, grids, args.precision, args, stream, seed=1 + rank)
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up: thermalisation sweeps (graph capture happens on the first call)
+    for _ in range(args.warmup):
+        ctx.sweep(0, S)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush_buf.zero_()                      # L2 flushed between timed steps
+            torch.cuda.synchronize()
+            ev[i][0].record(stream)
+            ctx.sweep(0, S)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * pps * S * args.steps / (total_ms * 1e-3)
+    stats = [ctx.get_stats(i) for i in range(len(grids))]
+    lib_ms = stats[0]["last_sweep_ms"]
+
+    # roofline of the sweep kernel: algorithmic work = 4 Lambda^2 flops per
+    # accepted flip (the rank-1-equivalent update of both spins), timed by the
+    # library's events around the persistent launch (the other three launches
+    # of a step are < 0.1% of it)
+    acc_per_step = sum(st["accept_rate"] * g[2] * g[3] * S for st, g in zip(stats, grids))
+    flops_step = sum(st["accept_rate"] * g[2] * g[3] * S * 4.0 * g[2] ** 2
+                     for st, g in zip(stats, grids))
+    pk, pk_kind = peaks()
+    tf32_peak = pk["bf16_tflops"] * (1.1 / 2.25)
+    achieved = flops_step / (statistics.median(step_ms) * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None,
+                "note": f"tf32 peak = {pk_kind} bf16 x 1.1/2.25 (nominal ratio); algorithmic "
+                        "4*Lambda^2 flops per accepted flip"}
+
+    # e2e through the C ABI from pinned host buffers: G0 upload (set_G0, which
+    # also rebuilds G in FP64 for every chain), sweeps, G(tau) download
+    pin_g0 = [torch.from_numpy(g).pin_memory() for g in g0]
+    pin_out = [torch.empty(g[2] + 1, dtype=torch.float64).pin_memory() for g in grids]
+    pin_err = [torch.empty(g[2] + 1, dtype=torch.float64).pin_memory() for g in grids]
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i in range(len(grids)):
+            hfqmc.load().hfqmc_set_G0(ctx.ctx, i, hfqmc.ctypes.c_void_p(pin_g0[i].data_ptr()))
+        ctx.sweep(0, S)
+        for i in range(len(grids)):
+            hfqmc.load().hfqmc_get_G(ctx.ctx, i, hfqmc.ctypes.c_void_p(pin_out[i].data_ptr()),
+                                     hfqmc.ctypes.c_void_p(pin_err[i].data_ptr()))
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * pps * S * e2e_steps / e2e_s, "unit": "proposals/s",
+           "h2d_bytes_per_step": int(sum(8 * g[2] for g in grids)),
+           "d2h_bytes_per_step": int(sum(16 * (g[2] + 1) for g in grids))}
+
+    extra = {}
+    if rank == 0 and not args.no_baselines:
+        # FP64 rank-1 GPU path on the same workload (shorter run: FP64 is slow here)
+        S64 = max(2, S // 50)
+        ctx64, _ = make_ctx(hfqmc, inputs, beta, grids, "f64_rank1", argparse.Namespace(
+            k=0, n_wrap=args.n_wrap, flush="auto"), stream, seed=1)
+        ctx64.sweep(0, 1)
+        ctx64.sweep(0, S64)
+        ms64 = ctx64.get_stats(0)["last_sweep_ms"]
+        extra["fp64_rank1"] = {"value": pps * S64 / (ms64 * 1e-3), "unit": "proposals/s",
+                               "sweeps": S64, "speedup_fp32_delayed": value / (pps * S64 / (ms64 * 1e-3))}
+        ctx64.close()
+        extra["cpu_baseline"] = oracle_sample(grids, beta, args.cpu_seconds)
+    line = {"metric": "HS flip proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (Bethe W=4 bath, half filling)",
+            "config": {"workload": args.workload, "beta": beta, "U": sorted({g[0] for g in grids}),
+                       "grids_L": [g[2] for g in grids], "chains": [g[3] for g in grids],
+                       "sweeps_per_step": S, "precision": args.precision,
+                       "k": [st["k"] for st in stats], "n_wrap": [st["n_wrap"] for st in stats],
+                       "l2": "flushed (512 MiB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(), "lib_last_sweep_ms": lib_ms,
+            "accept_rate": [round(st["accept_rate"], 4) for st in stats],
+            "drift_max": [st["drift_max"] for st in stats],
+            "recomputes": [st["recomputes"] for st in stats], **extra}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

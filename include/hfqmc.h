@@ -1,0 +1,186 @@
+/*
+ * hfqmc.h -- C ABI of the GB300 Hirsch-Fye QMC sweep library (libhfqmc.so).
+ *
+ * The library solves the fixed-bath impurity problem of the paper's
+ * "Multigrid HF-QMC method" section: for one bath Green function G0 it runs
+ * Hirsch-Fye QMC on several imaginary-time grids dtau_i at once, with many
+ * independent Markov chains per grid ("the raw Green functions G_dtau_i are
+ * averaged over 10-20 impurity solutions"), and returns the measured G(tau)
+ * with error bars per grid.  The dtau -> 0 extrapolation, Fourier transforms
+ * and the DMFT self-consistency are host-side glue above this ABI.
+ *
+ * Method (introduction of the paper: Trotter slicing into Lambda = beta/dtau
+ * slices, binary Hubbard-Stratonovich field s_l = +-1, Monte Carlo sampling;
+ * equations of Hirsch & Fye 1986, which the paper cites for the method):
+ *   cosh(lambda) = exp(dtau U / 2),  V^sigma_l = sigma lambda s_l,
+ *   G^sigma = [1 + (1 - G0)(e^{V^sigma} - 1)]^{-1} G0,
+ *   flip ratio R = R^up R^dn,  R^sigma = 1 + (1 - G^sigma_ll) Delta^sigma_l,
+ *   Delta^sigma_l = e^{-2 sigma lambda s_l} - 1,
+ *   accepted flip: G'_ij = G_ij + (G_il - delta_il) Delta G_lj / R^sigma.
+ * Matrices use the positive convention g_ll' = <T c(tau_l) c^+(tau_l')> with
+ * g_ll = 1 - n; the returned physical G(tau) = -g(tau).
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ * (l, sweep, chain, grid) for the proposal at slice l; u = 53-bit uniform from
+ * output words 0 and 1.  Initial field: s_l = +1 iff bit 0 of word 0 of the
+ * counter (l | 2^16, 0, chain, grid) is set.
+ *
+ * Conventions for every call:
+ *  - Return value: HFQMC_OK (0) or a negative HFQMC_E* code; the message is
+ *    then available from hfqmc_last_error(ctx).
+ *  - Host arrays are owned by the caller and only read/written during the
+ *    call; the library copies what it keeps.  Device memory belongs to the
+ *    context (optionally obtained through caller-supplied allocator hooks).
+ *  - One context per host thread; calls on one context must not overlap.
+ *  - All device work is ordered on the context's CUDA stream.
+ */
+#ifndef HFQMC_H
+#define HFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HFQMC_OK        0
+#define HFQMC_EINVAL   (-1) /* bad argument (beta/dtau not integral, grid out of range, ...) */
+#define HFQMC_ENOMEM   (-2) /* device or host allocation failed */
+#define HFQMC_ECUDA    (-3) /* a CUDA call failed (message holds the CUDA error string) */
+#define HFQMC_ESTATE   (-4) /* call out of order (e.g. sweep before every grid has a G0) */
+#define HFQMC_EDRIFT   (-5) /* max |G_fast - G_fresh| exceeded opts.drift_fail */
+#define HFQMC_ENUMERIC (-6) /* non-finite or non-positive weight ratio, singular pivot */
+#define HFQMC_ETIMEOUT (-7) /* a bounded device wait gave up */
+
+/* ---- options ------------------------------------------------------------ */
+enum {
+    HFQMC_F64_RANK1 = 0,   /* FP64 G, rank-1 update per accepted flip (baseline) */
+    HFQMC_F32_RANK1 = 1,   /* FP32 G, rank-1 update per accepted flip            */
+    HFQMC_F32_DELAYED = 2  /* FP32 G, k accepted flips gathered into one rank-k
+                              update (split-TF32 tensor-core GEMM)                */
+};
+enum { HFQMC_METROPOLIS = 0, HFQMC_HEAT_BATH = 1 };
+enum {
+    HFQMC_FLUSH_AUTO = 0,    /* tensor cores where available                    */
+    HFQMC_FLUSH_TCGEN05 = 1, /* rank-k flush on tcgen05 (kind::tf32, 3 passes)  */
+    HFQMC_FLUSH_FFMA = 2     /* rank-k flush on FP32 FMA (CUDA cores)           */
+};
+
+typedef void *(*hfqmc_alloc_fn)(size_t bytes, void *user);
+typedef void (*hfqmc_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int precision;      /* HFQMC_F64_RANK1 | HFQMC_F32_RANK1 | HFQMC_F32_DELAYED    */
+    int k;              /* delay depth for F32_DELAYED (8..64, multiple of 8); 0 = per-Lambda table */
+    int n_wrap;         /* FP64 recompute every n_wrap accepted flips; 0 = per-Lambda table; <0 = never */
+    int accept_rule;    /* HFQMC_METROPOLIS (accept iff u < R) | HFQMC_HEAT_BATH (u (1+R) < R) */
+    double drift_warn;  /* recorded only */
+    double drift_fail;  /* hfqmc_sweep returns HFQMC_EDRIFT above this (<= 0: never) */
+    void *cuda_stream;  /* cudaStream_t to order all work on; NULL = library-owned stream */
+    int autotune;       /* 1: use the autotuned per-Lambda table for k / n_wrap when 0 */
+    int flush;          /* HFQMC_FLUSH_* (F32_DELAYED only) */
+    int use_graph;      /* 1: replay hfqmc_sweep's launches as a captured CUDA graph */
+    hfqmc_alloc_fn alloc; /* optional device allocator hook (e.g. PyTorch's caching allocator) */
+    hfqmc_free_fn free;
+    void *alloc_user;
+    int resident_kb;    /* shared-memory budget (KiB per CTA) for keeping a chain's G on chip:
+                           0 = default (200), < 0 = never (G stays in HBM/L2) */
+    int gj_smem;        /* FP64 recompute on [A | M] in shared memory when it fits (Lambda <= 118):
+                           0 = yes, < 0 = never (HBM workspace; lower shared-memory footprint) */
+} hfqmc_opts;
+
+/* Per-grid statistics (hfqmc_get_stats). */
+typedef struct {
+    int L;                  /* Lambda = beta/dtau */
+    int chains;
+    int k;                  /* delay depth in use (1 for rank-1 paths) */
+    int n_wrap;             /* recompute interval in use */
+    int64_t sweeps;         /* sweeps done per chain since the first set_G0 */
+    int64_t proposals;      /* summed over chains */
+    int64_t accepted;
+    int64_t recomputes;
+    int64_t numeric_errors; /* proposals with R <= 0 or non-finite R */
+    double accept_rate;
+    double drift_max;       /* max |G_fast - G_fresh| over recomputes since set_G0 */
+    double last_sweep_ms;   /* device time of the last hfqmc_sweep (whole batch) */
+} hfqmc_stats;
+
+typedef struct hfqmc_ctx hfqmc_ctx;
+
+/* Fills *opts with defaults: F32_DELAYED, k = 0, n_wrap = 0 (table), Metropolis,
+ * drift_warn 1e-6, drift_fail 1e-3, own stream, autotune on, flush auto,
+ * graphs on, no allocator hooks. */
+void hfqmc_default_opts(hfqmc_opts *opts);
+
+/* Creates a context for one beta and one U over n_grids dtau grids.
+ * dtau[i]: grid spacing; Lambda_i = beta/dtau_i must be an integer
+ *          (|beta/dtau_i - Lambda_i| < 1e-9), 1 <= Lambda_i <= 1024.
+ * chains_per_grid[i] >= 1 independent chains on grid i.
+ * seed: Philox key.  opts may be NULL (defaults).
+ * Allocates all device state; no kernel runs until hfqmc_set_G0.
+ * On error *out is NULL and the code is returned (message via hfqmc_last_error(NULL)). */
+int hfqmc_create(hfqmc_ctx **out, double beta, double U, const double *dtau, int n_grids,
+                 const int *chains_per_grid, uint64_t seed, const hfqmc_opts *opts);
+
+/* As hfqmc_create, but grid i has its own interaction U[i] (several U values
+ * batched in one launch); "grid" in every other call indexes these pairs. */
+int hfqmc_create_ex(hfqmc_ctx **out, double beta, const double *U, const double *dtau,
+                    int n_grids, const int *chains_per_grid, uint64_t seed,
+                    const hfqmc_opts *opts);
+
+/* Sets the bath of grid `grid` from Lambda samples G0_tau[k] = G0(k dtau),
+ * k = 0..Lambda-1, physical sign, G0_tau[0] = G0(0+) (host array, copied).
+ * Builds the antiperiodic bath matrix M_ll' = -G0(tau_{l-l'}) (l >= l'),
+ * +G0(tau_{l-l'+Lambda}) (l < l'), then for every chain of the grid computes
+ * G^sigma = [1 + (1 - M)(e^V - 1)]^{-1} M by FP64 Gauss-Jordan elimination.
+ * First call for a grid: the field is drawn from Philox.  Later calls keep
+ * each chain's field, sweep counter and flip counters, rebuild G from the new
+ * bath and zero the measurement accumulators. */
+int hfqmc_set_G0(hfqmc_ctx *ctx, int grid, const double *G0_tau);
+
+/* Runs n_warm unmeasured then n_meas measured sweeps (one proposal per slice
+ * l = 0..Lambda-1 in order per sweep) on every chain of every grid, as one
+ * persistent launch over a longest-Lambda-first work queue.  Measured sweeps
+ * accumulate g^sigma(tau_k) = (1/Lambda) sum_l sgn G^sigma_{(l+k) mod Lambda, l}
+ * (sgn = -1 when l + k >= Lambda) and D = (1/Lambda) sum_l n^up_l n^dn_l.
+ * Then reduces chains per grid.  Blocks until the stream is done.
+ * Requires hfqmc_set_G0 on every grid (HFQMC_ESTATE otherwise). */
+int hfqmc_sweep(hfqmc_ctx *ctx, int64_t n_warm, int64_t n_meas);
+
+/* Measured G(tau_k), k = 0..Lambda-1, and G(beta-) = -1 - G(0+) at index Lambda
+ * (caller arrays of Lambda+1 doubles; G_err may be NULL).  Error: sample
+ * standard deviation (n-1) of the chain means over sqrt(n_chains); for one
+ * chain the measured sweeps of each hfqmc_sweep call are cut into 32
+ * consecutive bins and the same estimator is applied to the bin means. */
+int hfqmc_get_G(hfqmc_ctx *ctx, int grid, double *G_tau, double *G_err);
+
+/* Double occupancy D = <n_up n_dn> and its error bar (same estimator). */
+int hfqmc_get_D(hfqmc_ctx *ctx, int grid, double *D, double *D_err);
+
+int hfqmc_get_stats(hfqmc_ctx *ctx, int grid, hfqmc_stats *out);
+
+/* Lambda of a grid. */
+int hfqmc_grid_size(hfqmc_ctx *ctx, int grid, int *L);
+
+/* One chain's state, for parity tests: field s (Lambda int8), G^up and G^dn
+ * (Lambda x Lambda row-major doubles, converted from the working precision),
+ * counters[6] = {proposals, accepted, recomputes, decision hash, bad-ratio
+ * proposals, sweep index} and acc (2 Lambda sums of g^sigma(tau_k), spin-major).
+ * The decision hash is FNV-1a 64 (offset 0xcbf29ce484222325, prime
+ * 0x100000001b3) over sweep*Lambda + l of every accepted flip, in order.
+ * Any output pointer may be NULL. */
+int hfqmc_get_chain(hfqmc_ctx *ctx, int grid, int chain, int8_t *s, double *G_up,
+                    double *G_dn, int64_t *counters, double *acc);
+
+/* Message of the last failed call on ctx (or of the last failed create when ctx is NULL). */
+const char *hfqmc_last_error(const hfqmc_ctx *ctx);
+
+/* Frees all device and host state.  NULL is ignored. */
+void hfqmc_destroy(hfqmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFQMC_H */

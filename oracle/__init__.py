@@ -311,12 +311,27 @@ class OracleHFQMC:
         self.chains = [None] * len(self.grids)
 
     def set_G0(self, grid, G0_tau):
+        """First call: fresh chains (field from Philox).  Later calls keep each
+        chain's field, sweep index and flip counters, rebuild G from the new
+        bath and zero the measurement sums (the library's semantics)."""
         g = self.grids[grid]
         G0_tau = np.asarray(G0_tau, dtype=np.float64)
         assert G0_tau.shape == (g["L"],)
         M = bath_matrix(G0_tau)
-        self.chains[grid] = [Chain.new(M, g["lmbda"], self.seed, c, grid)
-                             for c in range(self.chains_per_grid[grid])]
+        if self.chains[grid] is None:
+            self.chains[grid] = [Chain.new(M, g["lmbda"], self.seed, c, grid)
+                                 for c in range(self.chains_per_grid[grid])]
+            return
+        for ch in self.chains[grid]:
+            ch.M = np.ascontiguousarray(M)
+            ch.Gup, _ = green(M, ch.s, ch.lmbda, 1)
+            ch.Gdn, _ = green(M, ch.s, ch.lmbda, -1)
+            ch.acc[:] = 0.0
+            ch.accD[:] = 0.0
+            ch.bins[:] = 0.0
+            ch.bin_counts[:] = 0
+            ch.n_meas = 0
+            ch.drift = 0.0
 
     def sweep(self, n_warm, n_meas):
         allc = [c for cs in self.chains for c in cs]

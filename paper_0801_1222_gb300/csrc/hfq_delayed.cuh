@@ -1,0 +1,454 @@
+// Support of the delayed (rank-k) FP32 sweep: shared-memory layout, FP32
+// flip ratio, and the two flush engines for G += U W^T:
+//   * flush_tcgen05 -- 5th-generation tensor cores.  Per spin and per
+//     128 x 128 output tile: the panels are split into TF32 hi/lo parts in
+//     shared memory (K-major, no swizzle, 8-row x 16-byte core matrices), one
+//     thread issues tcgen05.mma kind::tf32 (M=128, N<=128, K=8 per
+//     instruction) for hi*hi + hi*lo + lo*hi into a TMEM accumulator,
+//     commits to an mbarrier, and all warps read the tile back with
+//     tcgen05.ld and add it to G.  The dropped lo*lo term and the TF32
+//     rounding of lo leave a relative error ~2^-21 per product.
+//   * flush_ffma -- FP32 FMA on the CUDA cores (4 x 4 register tiles).
+#pragma once
+#include <cstdint>
+
+#include "hfq_device.cuh"
+
+namespace hfq {
+
+constexpr int kDelNT = 256;          // threads per CTA (8 warps)
+constexpr int kTmemCols = 128;       // TMEM columns per CTA (<= 4 CTAs per SM)
+constexpr int kTileN = 128;          // output tile: 128 rows x 128 columns
+
+struct DelLayout {
+  int ldS;      // row pitch of shared-memory G (floats)
+  int KP;       // row pitch of the FP32 panels (floats)
+  int K8;       // k rounded up to 8 (tf32 MMA K step)
+  // head (kept through a recompute): colk, u, s; body: stage, G, panels, diag
+  size_t off_colk, off_u, off_s, off_body;
+  size_t off_stage, off_G, off_U, off_W, off_diag, bytes;
+};
+
+__host__ __device__ inline size_t del_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// stage: A hi, A lo (128 x K8 each), B hi, B lo (128 x K8 each), tf32 in core-matrix layout
+__host__ __device__ inline size_t del_stage_bytes(int K) {
+  const int K8 = (K + 7) / 8 * 8;
+  return 4 * (size_t)kTileN * K8 * 4;
+}
+
+__host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem) {
+  DelLayout d;
+  d.ldS = L | 1;
+  d.KP = K + 1;  // odd pitch: a warp reading 32 rows hits 32 banks
+  d.K8 = (K + 7) / 8 * 8;
+  size_t o = 0;
+  d.off_colk = o;
+  o += del_align((size_t)L * 8, 128);
+  d.off_u = o;
+  o += del_align((size_t)L * 4, 128);
+  d.off_s = o;
+  o += del_align((size_t)L, 128);
+  o = del_align(o, 1024);
+  d.off_body = o;
+  d.off_stage = o;
+  // the staging area doubles as the measurement's per-warp partial sums
+  const size_t part = 2 * (size_t)(kDelNT / 32) * L * 4;
+  o += del_align(del_stage_bytes(K) > part ? del_stage_bytes(K) : part, 1024);
+  d.off_G = o;
+  if (resident) o += del_align(2 * (size_t)L * d.ldS * 4, 128);
+  d.off_U = o;
+  o += del_align(2 * (size_t)L * d.KP * 4, 128);
+  d.off_W = o;
+  o += del_align(2 * (size_t)L * d.KP * 4, 128);
+  d.off_diag = o;
+  o += del_align(2 * (size_t)L * 4, 128);
+  if (gj_smem && d.off_body + gj_smem_bytes(L) > o) o = d.off_body + gj_smem_bytes(L);
+  d.bytes = o;
+  return d;
+}
+
+__device__ __forceinline__ bool del_decide(const GridConst& gc, float gu, float gd, int sl, float u,
+                                           int rule, bool* bad) {
+  const float du = sl > 0 ? gc.deltaf[0] : gc.deltaf[1];
+  const float dd = sl > 0 ? gc.deltaf[1] : gc.deltaf[0];
+  const float Ru = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gu), du));
+  const float Rd = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gd), dd));
+  const float R = __fmul_rn(Ru, Rd);
+  *bad = !(R > 0.f) || !isfinite(R);
+  return rule == 0 ? (u < R) : (__fmul_rn(u, __fadd_rn(1.f, R)) < R);
+}
+
+__device__ __forceinline__ void del_factors(const GridConst& gc, float gu, float gd, int sl, float* fu,
+                                            float* fd) {
+  const float du = sl > 0 ? gc.deltaf[0] : gc.deltaf[1];
+  const float dd = sl > 0 ? gc.deltaf[1] : gc.deltaf[0];
+  const float Ru = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gu), du));
+  const float Rd = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gd), dd));
+  *fu = du / Ru;
+  *fd = dd / Rd;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 FMA flush: G^sigma[i][c] += sum_{m<j} U^sigma[i][m] W^sigma[c][m]
+// ---------------------------------------------------------------------------
+__device__ inline void flush_ffma(float* Gu, float* Gd, int ld, const float* Pu, const float* Pw,
+                                  int KP, int L, int j) {
+  const int T4 = (L + 3) / 4;
+  const int tiles = T4 * T4;
+  for (int sp = 0; sp < 2; ++sp) {
+    float* G = sp ? Gd : Gu;
+    const float* U = Pu + (size_t)sp * L * KP;
+    const float* W = Pw + (size_t)sp * L * KP;
+    for (int t = threadIdx.x; t < tiles; t += kDelNT) {
+      const int i0 = (t / T4) * 4, c0 = (t % T4) * 4;
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+      for (int m = 0; m < j; ++m) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[r] = (i0 + r < L) ? U[(size_t)(i0 + r) * KP + m] : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bv[c] = (c0 + c < L) ? W[(size_t)(c0 + c) * KP + m] : 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = __fmaf_rn(av[r], bv[c], acc[r][c]);
+      }
+      float gv[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          gv[r][c] = (i0 + r < L && c0 + c < L) ? G[(size_t)(i0 + r) * ld + c0 + c] : 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (i0 + r < L && c0 + c < L) G[(size_t)(i0 + r) * ld + c0 + c] = gv[r][c] + acc[r][c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 (5th-gen tensor core) helpers, inline PTX for sm_100a / sm_103a
+// ---------------------------------------------------------------------------
+struct TcState {
+  uint32_t tmem;       // TMEM base address of this CTA's allocation
+  uint32_t mbar;       // shared address of the completion mbarrier
+  uint32_t phase;      // parity of the next completion
+  int failed;          // a wait gave up: the tensor path is not used again
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t f32_to_tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// K-major, no-swizzle canonical layout: element (r, m) of a rows x K8 tile
+// lives at (r/8)*SBO + (m/4)*LBO + (r%8)*16 + (m%4)*4 bytes, with the
+// 8-row x 16-byte core matrices contiguous along K (LBO = 128 B) and the
+// 8-row groups SBO = (K8/4)*128 B apart.
+__device__ __forceinline__ uint32_t core_offset(int r, int m, int K8) {
+  return (uint32_t)((r >> 3) * (K8 / 4) * 128 + (m >> 2) * 128 + (r & 7) * 16 + (m & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t make_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for sm_100-class parts
+  // base offset 0, absolute LBO mode off, layout type 0 = no swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128.
+__device__ __forceinline__ uint32_t make_idesc_tf32(int N) {
+  uint32_t d = 0;
+  d |= 1u << 4;                       // D format F32
+  d |= 2u << 7;                       // A format TF32
+  d |= 2u << 10;                      // B format TF32
+  d |= (uint32_t)(N >> 3) << 17;      // N / 8
+  d |= (uint32_t)(128 >> 4) << 24;    // M / 16
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                            uint32_t idesc, int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the mbarrier phase with a one-second limit; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(mbar, phase)) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Allocates kTmemCols TMEM columns (warp 0) and initialises the mbarrier.
+__device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long long* s_mbar,
+                                int* status) {
+  (void)status;
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tc->tmem = *s_tmem;
+  tc->mbar = smem_u32(s_mbar);
+  tc->phase = 0;
+  tc->failed = 0;
+}
+
+__device__ inline void tc_teardown(TcState* tc) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc->tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+// Writes rows [row0, row0+nrows) of a panel (pitch KP floats, j valid
+// columns) as TF32 hi and lo parts into 128-row core-matrix tiles; rows and
+// columns outside the valid range are zero.
+__device__ __forceinline__ void stage_split(const float* P, int KP, int row0, int nrows, int j, int K8,
+                                            unsigned char* hi, unsigned char* lo) {
+  const int chunks = kTileN * (K8 / 4);
+  for (int c = threadIdx.x; c < chunks; c += kDelNT) {
+    const int r = c / (K8 / 4), m0 = (c % (K8 / 4)) * 4;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = (r < nrows && m0 + q < j) ? P[(size_t)(row0 + r) * KP + m0 + q] : 0.f;
+      h[q] = f32_to_tf32_rna(x);
+      l[q] = f32_to_tf32_rna(x - __uint_as_float(h[q]));
+    }
+    const uint32_t off = core_offset(r, m0, K8);
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// Issues the 3-pass split-TF32 product of one 128 x N tile over K8 and waits.
+// Returns false if the completion wait gave up.
+__device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, const unsigned char* Alo,
+                                       const unsigned char* Bhi, const unsigned char* Blo, int K8,
+                                       int N16) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    const uint32_t sbo = (uint32_t)(K8 / 4) * 128u, lbo = 128u;
+    const uint32_t idesc = make_idesc_tf32(N16);
+    const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
+    const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+    int acc = 0;
+    for (int kb = 0; kb < K8 / 8; ++kb) {
+      const uint32_t koff = (uint32_t)kb * 256u;
+      tc_mma_tf32(tc->tmem, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo),
+                  idesc, acc);
+      acc = 1;
+      tc_mma_tf32(tc->tmem, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_lo + koff, lbo, sbo),
+                  idesc, 1);
+      tc_mma_tf32(tc->tmem, make_smem_desc(a_lo + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo),
+                  idesc, 1);
+    }
+    tc_commit(tc->mbar);
+  }
+  const bool ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
+  // every thread must take the same branch afterwards
+  const bool ok = !__syncthreads_or(ok_here ? 0 : 1);
+  tc->phase ^= 1u;
+  tc_fence_after();
+  return ok;
+}
+
+// G^sigma += U^sigma W^sigma^T via tcgen05, one 128 x 128 output tile at a
+// time.  The product is formed transposed, D = W U^T (A = 128 rows of W, B =
+// up to 128 rows of U), so TMEM lane m holds column nb+m of the G tile and
+// the 32 threads of a warp touch 32 consecutive columns of one G row per
+// access (coalesced in HBM, conflict-free in shared memory).
+__device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
+                                     const float* Pw, int KP, int L, int j, unsigned char* stage,
+                                     const DelLayout& lay, int* status) {
+  if (tc->failed) {
+    flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
+    return;
+  }
+  const int K8 = (j + 7) / 8 * 8;
+  const size_t tile_bytes = (size_t)kTileN * lay.K8 * 4;
+  unsigned char* Ahi = stage;
+  unsigned char* Alo = stage + tile_bytes;
+  unsigned char* Bhi = stage + 2 * tile_bytes;
+  unsigned char* Blo = stage + 3 * tile_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32*quarter.., columns 64*half..
+  for (int sp = 0; sp < 2; ++sp) {
+    float* G = sp ? Gd : Gu;
+    const float* U = Pu + (size_t)sp * L * KP;
+    const float* W = Pw + (size_t)sp * L * KP;
+    for (int nb = 0; nb < L; nb += kTileN) {         // block of G columns = rows of W
+      const int nN = min(kTileN, L - nb);
+      stage_split(W, KP, nb, nN, j, K8, Ahi, Alo);
+      for (int mb = 0; mb < L; mb += kTileN) {       // block of G rows = rows of U
+        const int nM = min(kTileN, L - mb);
+        const int N16 = (nM + 15) / 16 * 16;
+        stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
+        if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16)) {
+          // the tensor core did not signal completion within the limit: flag
+          // the context (the host returns HFQMC_ETIMEOUT) and use the CUDA
+          // cores for every later flush of this CTA
+          if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+          tc->failed = 1;
+          __syncthreads();
+          return;
+        }
+        const int m = 32 * quarter + lane;  // G column nb + m
+        for (int cb = 64 * half; cb < 64 * half + 64 && cb < N16; cb += 16) {
+          float v[16];
+          tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb, v);
+          if (m < nN) {
+            float* g = G + (size_t)(mb + cb) * ld + nb + m;
+            float gv[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) gv[q] = (cb + q < nM) ? g[(size_t)q * ld] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (cb + q < nM) g[(size_t)q * ld] = gv[q] + v[q];
+          }
+        }
+        tc_fence_before();
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l}, walked
+// row by row: element (r, l) belongs to k = r - l (sign +) or r - l + L
+// (sign -, antiperiodic wrap).  Each warp takes whole rows, lanes take
+// columns (coalesced), and accumulates into its own shared-memory row of
+// FP32 partial sums (no two lanes of a row share a k); the warps' partials
+// are added in a fixed order.  Everything stays on the FP32 pipe: the caller
+// folds the per-sweep totals into FP64 accumulators.
+// part: 2 * NW * L floats of shared scratch; out[k], out[L+k] receive the
+// sums (not yet divided by L).
+__device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, int L, float* part,
+                                    float* out) {
+  constexpr int NW = kDelNT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < 2 * NW * L; e += kDelNT) part[e] = 0.f;
+  __syncthreads();
+  for (int sp = 0; sp < 2; ++sp) {
+    const float* G = sp ? Gd : Gu;
+    float* pw = part + (size_t)(sp * NW + warp) * L;
+    for (int r = warp; r < L; r += NW) {
+      const float* gr = G + (size_t)r * ld;
+      for (int l = lane; l < L; l += 32) {
+        const float v = gr[l];
+        if (r >= l)
+          pw[r - l] += v;
+        else
+          pw[r - l + L] -= v;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * L; e += kDelNT) {
+    const int sp = e >= L, k = e - sp * L;
+    float acc = 0.f;
+    for (int w = 0; w < NW; ++w) acc += part[(size_t)(sp * NW + w) * L + k];
+    out[e] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float block_sum_f(float v, float* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float r = 0.f;
+#pragma unroll
+  for (int w = 0; w < kDelNT / 32; ++w) r += red[w];
+  return r;
+}
+
+}  // namespace hfq

@@ -1,0 +1,166 @@
+// Device-side data layout of the HF-QMC sweep library (GB300, sm_103a).
+//
+// HBM layout (all per context, allocated once at create):
+//   per grid  : GridConst (Lambda, lambda, the two flip factors Delta and the
+//               two bath factors e^{+-lambda}-1), the FP64 bath matrix M
+//               (Lambda x Lambda row-major), GridAccount (measured-sweep
+//               counts, 32 bin counts), GridOut (reduced G(tau), errors, D).
+//   per chain : HS field s (int8[Lambda]), G^up and G^dn back to back
+//               (2 x Lambda x Lambda, row-major, FP64 or FP32), the FP64
+//               Gauss-Jordan workspace [A | M] (Lambda x 2 Lambda), the
+//               measurement sums (2 Lambda spin-major, 32 x Lambda bins,
+//               1 + 32 D sums) and ChainCounters.
+// Every chain is one work item; items are processed longest-Lambda-first
+// from an atomic queue by a persistent grid of CTAs.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hfq {
+
+constexpr int kBins = 32;
+constexpr unsigned long long kFnvOffset = 0xcbf29ce484222325ull;
+constexpr unsigned long long kFnvPrime = 0x100000001b3ull;
+
+// Status bits of the context-wide error word.
+constexpr int kStatusSingular = 1;   // zero pivot in a Gauss-Jordan recompute
+constexpr int kStatusNonFinite = 2;  // non-finite G after a recompute
+constexpr int kStatusTimeout = 4;    // a bounded wait gave up
+
+struct GridConst {
+  int L;           // Lambda
+  int chains;
+  int item0;       // first item (chain 0) of this grid
+  int resident;    // 1: G staged in shared memory for the whole chain
+  int k;           // delay depth (delayed path)
+  int n_wrap;      // recompute interval in accepted flips (<= 0: never)
+  int gj_smem;     // 1: the FP64 recompute works on [A | M] in shared memory
+  double lambda;   // cosh(lambda) = exp(dtau U / 2)
+  double delta[2]; // Delta for sigma*s = +1: e^{-2 lambda} - 1; sigma*s = -1: e^{2 lambda} - 1
+  double dV[2];    // e^{sigma lambda s} - 1 for sigma*s = +1 / -1
+  float deltaf[2]; // delta[] rounded to FP32 (the FP32 paths' flip factors)
+  const double* M; // bath matrix (FP64, L x L)
+};
+
+struct ChainCounters {
+  long long t;               // global index of the next sweep
+  long long proposals;
+  long long accepted;        // cumulative since the first set_G0 (drives n_wrap)
+  long long recomputes;
+  unsigned long long hash;   // FNV-1a over sweep*L + l of accepted flips
+  long long bad;             // proposals with R <= 0 or non-finite R
+  double drift;              // max |G_fast - G_fresh| since the last set_G0
+  int status;
+  int pad;
+};
+
+struct ItemPtrs {
+  int grid, chain, L, pad;
+  int8_t* s;
+  void* G;        // G^up then G^dn, L x L each, row-major
+  double* ws;     // L x 2L Gauss-Jordan workspace
+  double* acc;    // 2L
+  double* bins;   // 32 L
+  double* accD;   // 1 + 32
+  ChainCounters* cnt;
+};
+
+struct GridAccount {
+  long long n_meas;          // measured sweeps since set_G0
+  long long bin_count[kBins];
+};
+
+struct GridOut {
+  long long proposals, accepted, recomputes, bad;
+  double drift;
+  double D, D_err;
+  double pad;
+};
+
+struct SweepArgs {
+  const GridConst* grids;
+  const ItemPtrs* items;
+  const int* order;          // LPT order of items
+  int n_items;
+  int* queue_head;
+  int* status;               // context-wide error word (bit flags)
+  unsigned long long seed;
+  long long n_warm, n_meas;
+  int accept_rule;           // 0 Metropolis, 1 heat bath
+  int flush;                 // delayed path: 1 tcgen05, 2 FFMA
+};
+
+// Bytes of shared memory the FP64 recompute needs for [A | M] of size L.
+__host__ __device__ inline size_t gj_smem_bytes(int L) { return 2 * (size_t)L * L * sizeof(double); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with the round
+// multipliers, combined with the other words and the key by XOR; the key is
+// bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned long long seed) {
+  unsigned k0 = (unsigned)(seed & 0xffffffffull);
+  unsigned k1 = (unsigned)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// 53-bit uniform in [0,1) from words 0 and 1 (all steps exact in FP64).
+__device__ __forceinline__ double u53(unsigned x0, unsigned x1) {
+  return __dmul_rn(__dadd_rn(__dmul_rn((double)(x0 >> 5), 67108864.0), (double)(x1 >> 6)),
+                   1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ double proposal_uniform(int l, long long t, int chain, int grid,
+                                                   unsigned long long seed) {
+  const uint4 x = philox4x32_10(make_uint4((unsigned)l, (unsigned)t, (unsigned)chain,
+                                           (unsigned)grid), seed);
+  return u53(x.x, x.y);
+}
+
+__device__ __forceinline__ int8_t initial_spin(int l, int chain, int grid,
+                                               unsigned long long seed) {
+  const uint4 x = philox4x32_10(make_uint4((unsigned)l | (1u << 16), 0u, (unsigned)chain,
+                                           (unsigned)grid), seed);
+  return (x.x & 1u) ? (int8_t)1 : (int8_t)-1;
+}
+
+// Block-wide max of a non-negative double; every thread gets the result.
+// red: NT/32 doubles of shared scratch.  Contains barriers.
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) r = fmax(r, red[w]);
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) r += red[w];
+  return r;
+}
+
+}  // namespace hfq

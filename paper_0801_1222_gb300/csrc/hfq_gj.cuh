@@ -1,0 +1,166 @@
+// FP64 recomputation of the Green matrices from the field:
+//   G^sigma = A^{-1} M,  A^sigma = 1 + (1 - M) diag(e^{sigma lambda s} - 1),
+// the Dyson equation that links the interacting G to the bath G0 (= M) in
+// Hirsch-Fye QMC.  It is the only FP64 step of the FP32 sweep paths and is
+// followed by the drift check max |G_fast - G_fresh|.
+//
+// Algorithm: Gauss-Jordan elimination with partial pivoting on the augmented
+// L x 2L matrix [A | M] held in the chain's HBM workspace (L2-resident for
+// the sizes used).  One CTA; per pivot column three barriers (pivot search,
+// row swap + scale, elimination).  Cost 1.5 L^3 DFMA per spin, bound by the
+// FP64 pipe (about 2 DFMA/clk/SM on GB300).
+#pragma once
+#include "hfq_device.cuh"
+
+namespace hfq {
+
+// In-place Gauss-Jordan on W = [A | B] (L rows, 2L columns, row-major), in
+// shared or global memory.  colk: L doubles of shared scratch (the pivot
+// column of the current step, so the elimination reads it once per row).
+// The elimination keeps the pivot row in registers and issues the loads of
+// kGjChunk columns of a row before any of their stores, so a warp has that
+// many independent accesses in flight even when W lives in L2.
+// On return the right half holds A^{-1} B.  Returns -1 on a zero pivot
+// (uniformly in all threads), 0 otherwise.
+constexpr int kGjChunk = 8;
+
+template <int NT>
+__device__ int gj_eliminate(double* W, int L, double* red, int* redi, double* s_inv, int* s_piv,
+                            double* colk) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ld = 2 * L;
+  for (int k = 0; k < L; ++k) {
+    double best = -1.0;
+    int bi = L;
+    for (int i = k + tid; i < L; i += NT) {
+      const double v = fabs(W[(size_t)i * ld + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red[warp] = best;
+      redi[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = red[0];
+      int p = redi[0];
+      for (int w = 1; w < NW; ++w)
+        if (red[w] > b || (red[w] == b && redi[w] < p)) {
+          b = red[w];
+          p = redi[w];
+        }
+      if (!(b > 0.0) || p >= L) {
+        *s_piv = -1;
+      } else {
+        *s_piv = p;
+        *s_inv = 1.0 / W[(size_t)p * ld + k];
+      }
+    }
+    __syncthreads();
+    const int p = *s_piv;
+    if (p < 0) return -1;
+    const double inv = *s_inv;
+    // swap rows k and p (columns >= k), scale the new row k; record column k
+    for (int j = k + tid; j < ld; j += NT) {
+      const double a = W[(size_t)k * ld + j];
+      const double b = W[(size_t)p * ld + j];
+      W[(size_t)p * ld + j] = a;
+      W[(size_t)k * ld + j] = b * inv;
+      if (j == k) colk[p] = a;
+    }
+    for (int i = tid; i < L; i += NT)
+      if (i != k && i != p) colk[i] = W[(size_t)i * ld + k];
+    __syncthreads();
+    // eliminate column k from every other row
+    const int j0 = k + 1;
+    const double* wk = W + (size_t)k * ld;
+    for (int c0 = j0; c0 < ld; c0 += 32 * kGjChunk) {
+      double rk[kGjChunk];
+#pragma unroll
+      for (int c = 0; c < kGjChunk; ++c) {
+        const int j = c0 + lane + 32 * c;
+        rk[c] = j < ld ? wk[j] : 0.0;
+      }
+      for (int i = warp; i < L; i += NW) {
+        if (i == k) continue;
+        const double f = colk[i];
+        if (f == 0.0) continue;
+        double* wi = W + (size_t)i * ld;
+        double v[kGjChunk];
+#pragma unroll
+        for (int c = 0; c < kGjChunk; ++c) {
+          const int j = c0 + lane + 32 * c;
+          v[c] = j < ld ? wi[j] : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < kGjChunk; ++c) {
+          const int j = c0 + lane + 32 * c;
+          if (j < ld) wi[j] = fma(-f, rk[c], v[c]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// Recomputes G^up and G^dn (working precision T, leading dimension ldG) for
+// the field s.  Returns max |G_old - G_new| over both spins when with_drift,
+// 0 otherwise, and -1 after a zero pivot (status bit set).
+template <typename T, int NT>
+__device__ double recompute_green(const GridConst& gc, const int8_t* s, T* Gup, T* Gdn, int ldG,
+                                  double* W, double* red, int* redi, double* s_inv, int* s_piv,
+                                  double* colk, bool with_drift, int* status_word) {
+  constexpr int NW = NT / 32;
+  const int L = gc.L, ld = 2 * L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double dmax = 0.0;
+  bool finite = true;
+  for (int sp = 0; sp < 2; ++sp) {
+    T* G = sp ? Gdn : Gup;
+    const int sig = sp ? -1 : 1;
+    for (int i = warp; i < L; i += NW) {
+      const double* Mi = gc.M + (size_t)i * L;
+      double* Wi = W + (size_t)i * ld;
+      for (int j = lane; j < L; j += 32) {
+        const double m = Mi[j];
+        const double d = (sig * (int)s[j] > 0) ? gc.dV[0] : gc.dV[1];
+        const double e = (i == j) ? 1.0 : 0.0;
+        Wi[j] = e + (e - m) * d;
+        Wi[L + j] = m;
+      }
+    }
+    __syncthreads();
+    if (gj_eliminate<NT>(W, L, red, redi, s_inv, s_piv, colk) != 0) {
+      if (tid == 0) atomicOr(status_word, kStatusSingular);
+      return -1.0;
+    }
+    for (int i = warp; i < L; i += NW) {
+      const double* Wi = W + (size_t)i * ld + L;
+      T* Gi = G + (size_t)i * ldG;
+      for (int j = lane; j < L; j += 32) {
+        const double gn = Wi[j];
+        if (with_drift) dmax = fmax(dmax, fabs((double)Gi[j] - gn));
+        finite = finite && isfinite(gn);
+        Gi[j] = (T)gn;
+      }
+    }
+    __syncthreads();
+  }
+  if (!finite) atomicOr(status_word, kStatusNonFinite);
+  return with_drift ? block_max<NT>(dmax, red) : 0.0;
+}
+
+}  // namespace hfq

@@ -1,0 +1,32 @@
+// Host-side launchers of the sweep library's kernels (C++ linkage, internal).
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "hfq_device.cuh"
+
+namespace hfq {
+
+// bath matrix M of one grid from G0(tau_k)
+int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st);
+// initial (or refreshed) field and Green matrices of the chains of one grid
+int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item0, int n_chains,
+                       int L, bool f64, bool first_time, bool gj_smem, cudaStream_t st);
+// measured-sweep bookkeeping of every grid for one hfqmc_sweep call
+int launch_account(GridAccount* acc, int n_grids, long long n_meas, cudaStream_t st);
+// per-grid mean over chains and error bars
+int launch_reduce(const GridConst* grids, const ItemPtrs* items, const GridAccount* acc,
+                  GridOut* gout, double* outG, double* outErr, const long long* out_off,
+                  int n_grids, cudaStream_t st);
+
+// rank-1 sweep (FP64 baseline / FP32)
+size_t rank1_smem(int L, bool resident, bool f64, bool gj_smem);
+int rank1_config(bool f64, size_t smem, int* threads, int* ctas_per_sm);
+int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
+
+// delayed rank-k sweep (FP32)
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem);
+int delayed_config(size_t smem, int* threads, int* ctas_per_sm);
+int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
+
+}  // namespace hfq

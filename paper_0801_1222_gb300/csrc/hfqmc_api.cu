@@ -1,0 +1,663 @@
+// Host runtime of the C ABI declared in include/hfqmc.h.
+//
+// A context owns all device state of one batch of (U, dtau) grids x chains,
+// laid out grid-major so that every per-grid reset is one contiguous memset.
+// hfqmc_sweep enqueues, on the context stream, the whole hot path as four
+// launches -- queue reset, measured-sweep bookkeeping, the persistent sweep
+// kernel over all chains of all grids, the per-grid reduction -- plus one
+// small device-to-host copy of the per-grid counters; with use_graph these
+// are captured once per (n_warm, n_meas) and replayed as a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hfqmc.h"
+#include "hfq_device.cuh"
+#include "hfq_launch.h"
+
+using namespace hfq;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct GridHost {
+  double U, dtau, lambda;
+  int L, chains, item0, k, n_wrap, resident, gj_smem;
+  bool g0_set = false, ever_set = false;
+  long long out_off;
+};
+
+// Per-Lambda defaults of the delay depth and recompute interval (the
+// autotuner's table; see autotune.py, which measures and rewrites it).
+struct TuneEntry {
+  int L_max, k, n_wrap;
+};
+const TuneEntry kTuneTable[] = {
+    {64, 8, 1024},    {128, 16, 2048},  {192, 32, 4096},
+    {256, 32, 4096},  {384, 64, 8192},  {1024, 64, 8192},
+};
+
+void tune_lookup(int L, int* k, int* n_wrap) {
+  for (const auto& e : kTuneTable)
+    if (L <= e.L_max) {
+      *k = e.k;
+      *n_wrap = e.n_wrap;
+      return;
+    }
+  *k = 64;
+  *n_wrap = 8192;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct hfqmc_ctx {
+  int device = 0, n_sm = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  hfqmc_opts opts;
+  double beta = 0.0;
+  uint64_t seed = 0;
+  int n_grids = 0, n_items = 0;
+  std::vector<GridHost> gh;
+  std::vector<GridConst> gc;
+  std::vector<ItemPtrs> items;
+  std::vector<void*> allocs;
+  // device
+  GridConst* d_grids = nullptr;
+  ItemPtrs* d_items = nullptr;
+  int* d_order = nullptr;
+  int* d_queue = nullptr;
+  int* d_status = nullptr;
+  double* d_G0 = nullptr;
+  GridAccount* d_account = nullptr;
+  GridOut* d_gout = nullptr;
+  double* d_outG = nullptr;
+  double* d_outErr = nullptr;
+  long long* d_out_off = nullptr;
+  unsigned char* d_pool = nullptr;
+  // pinned host mirrors
+  GridOut* h_gout = nullptr;
+  int* h_status = nullptr;
+  // sweep launch shape
+  size_t sweep_smem = 0;
+  int sweep_ctas = 0;
+  std::map<std::pair<long long, long long>, cudaGraphExec_t> graphs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double last_ms = 0.0;
+  long long sweeps_done = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(hfqmc_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(hfqmc_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, HFQMC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+void* dev_alloc(hfqmc_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (c->opts.alloc) {
+    p = c->opts.alloc(bytes, c->opts.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+bool f64_path(const hfqmc_ctx* c) { return c->opts.precision == HFQMC_F64_RANK1; }
+size_t elem_size(const hfqmc_ctx* c) { return f64_path(c) ? sizeof(double) : sizeof(float); }
+
+int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
+  SweepArgs a;
+  a.grids = c->d_grids;
+  a.items = c->d_items;
+  a.order = c->d_order;
+  a.n_items = c->n_items;
+  a.queue_head = c->d_queue;
+  a.status = c->d_status;
+  a.seed = c->seed;
+  a.n_warm = n_warm;
+  a.n_meas = n_meas;
+  a.accept_rule = c->opts.accept_rule;
+  a.flush = c->opts.flush;
+  if (c->opts.precision == HFQMC_F32_DELAYED)
+    return launch_sweep_delayed(a, c->sweep_ctas, c->sweep_smem, c->stream);
+  return launch_sweep_rank1(f64_path(c), a, c->sweep_ctas, c->sweep_smem, c->stream);
+}
+
+// The whole hot path of one hfqmc_sweep call, enqueued on the context stream.
+int enqueue_sweep(hfqmc_ctx* c, long long n_warm, long long n_meas) {
+  cudaError_t e = cudaMemsetAsync(c->d_queue, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(queue)");
+  int r = launch_account(c->d_account, c->n_grids, n_meas, c->stream);
+  if (r) return cuda_fail(c, (cudaError_t)r, "launch_account");
+  r = launch_sweep_kernel(c, n_warm, n_meas);
+  if (r) return cuda_fail(c, (cudaError_t)r, "sweep kernel launch");
+  r = launch_reduce(c->d_grids, c->d_items, c->d_account, c->d_gout, c->d_outG, c->d_outErr,
+                    c->d_out_off, c->n_grids, c->stream);
+  if (r) return cuda_fail(c, (cudaError_t)r, "launch_reduce");
+  e = cudaMemcpyAsync(c->h_gout, c->d_gout, sizeof(GridOut) * c->n_grids,
+                      cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(gout)");
+  e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(status)");
+  return HFQMC_OK;
+}
+
+int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
+                const double* dtau, int n_grids, const int* chains, uint64_t seed,
+                const hfqmc_opts* opts) {
+  hfqmc_ctx* c = nullptr;
+  if (!out) return fail(nullptr, HFQMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, HFQMC_EINVAL, "beta must be > 0");
+  if (n_grids < 1 || n_grids > 4096) return fail(nullptr, HFQMC_EINVAL, "n_grids out of range");
+  if (!dtau || !chains || !U) return fail(nullptr, HFQMC_EINVAL, "NULL array argument");
+  hfqmc_opts o;
+  if (opts)
+    o = *opts;
+  else
+    hfqmc_default_opts(&o);
+  if (o.precision < HFQMC_F64_RANK1 || o.precision > HFQMC_F32_DELAYED)
+    return fail(nullptr, HFQMC_EINVAL, "unknown precision");
+  if (o.accept_rule != HFQMC_METROPOLIS && o.accept_rule != HFQMC_HEAT_BATH)
+    return fail(nullptr, HFQMC_EINVAL, "unknown accept_rule");
+  if (o.k != 0 && (o.k < 8 || o.k > 64 || o.k % 8 != 0))
+    return fail(nullptr, HFQMC_EINVAL, "k must be 0 or a multiple of 8 in [8, 64]");
+
+  std::vector<GridHost> gh(n_grids);
+  long long items = 0;
+  for (int g = 0; g < n_grids; ++g) {
+    const double Ug = per_grid_U ? U[g] : U[0];
+    if (!(dtau[g] > 0.0) || !std::isfinite(dtau[g]))
+      return fail(nullptr, HFQMC_EINVAL, "dtau must be > 0");
+    if (!(Ug >= 0.0) || !std::isfinite(Ug)) return fail(nullptr, HFQMC_EINVAL, "U must be >= 0");
+    const double Lr = beta / dtau[g];
+    const long long L = std::llround(Lr);
+    if (std::fabs(Lr - (double)L) > 1e-9 || L < 1 || L > 1024)
+      return fail(nullptr, HFQMC_EINVAL,
+                  "beta/dtau must be an integer Lambda in [1, 1024] (grid " + std::to_string(g) + ")");
+    if (chains[g] < 1 || chains[g] > (1 << 20))
+      return fail(nullptr, HFQMC_EINVAL, "chains_per_grid must be in [1, 2^20]");
+    gh[g].U = Ug;
+    gh[g].L = (int)L;
+    gh[g].dtau = beta / (double)L;
+    gh[g].lambda = std::acosh(std::exp(0.5 * gh[g].dtau * Ug));
+    gh[g].chains = chains[g];
+    gh[g].item0 = (int)items;
+    items += chains[g];
+  }
+  if (items > (1 << 22)) return fail(nullptr, HFQMC_EINVAL, "too many chains");
+
+  c = new (std::nothrow) hfqmc_ctx();
+  if (!c) return fail(nullptr, HFQMC_ENOMEM, "host allocation failed");
+  c->opts = o;
+  c->beta = beta;
+  c->seed = seed;
+  c->n_grids = n_grids;
+  c->n_items = (int)items;
+  c->gh = gh;
+
+  auto bail = [&](int code) {
+    g_create_error = c->err;
+    hfqmc_destroy(c);
+    return code;
+  };
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
+  e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaDeviceGetAttribute"));
+  if (o.cuda_stream) {
+    c->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+    c->own_stream = true;
+  }
+  if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaEventCreate"));
+
+  // per-grid constants, delay depth, recompute interval, residency
+  const bool f64 = f64_path(c);
+  const size_t es = elem_size(c);
+  size_t smem_max = 0;
+  const size_t kResidentBudget =
+      o.resident_kb == 0 ? 200 * 1024 : (o.resident_kb < 0 ? 0 : (size_t)o.resident_kb * 1024);
+  const size_t kSmemMax = 227 * 1024;
+  c->gc.resize(n_grids);
+  long long out_off = 0;
+  for (int g = 0; g < n_grids; ++g) {
+    GridHost& h = c->gh[g];
+    int k_t = 16, nw_t = 1024;
+    tune_lookup(h.L, &k_t, &nw_t);
+    h.k = (o.precision == HFQMC_F32_DELAYED) ? (o.k ? o.k : k_t) : 1;
+    h.n_wrap = o.n_wrap ? o.n_wrap : nw_t;
+    size_t sm;
+    // the FP64 recompute works in shared memory when [A | M] fits next to the head
+    h.gj_smem = o.gj_smem >= 0 && gj_smem_bytes(h.L) + 4 * (size_t)h.L * 8 + 1024 <= kSmemMax;
+    if (o.precision == HFQMC_F32_DELAYED) {
+      // the panels of both spins must fit in shared memory: lower k if needed
+      while (h.k > 8 && delayed_smem(h.L, h.k, false, h.gj_smem) > kSmemMax) h.k -= 8;
+      if (delayed_smem(h.L, h.k, false, h.gj_smem) > kSmemMax) {
+        g_create_error = "Lambda too large for the delayed path's shared-memory panels";
+        hfqmc_destroy(c);
+        return HFQMC_EINVAL;
+      }
+      sm = delayed_smem(h.L, h.k, true, h.gj_smem);
+      h.resident = sm <= kResidentBudget;
+      if (!h.resident) sm = delayed_smem(h.L, h.k, false, h.gj_smem);
+    } else {
+      sm = rank1_smem(h.L, true, f64, h.gj_smem);
+      h.resident = sm <= kResidentBudget;
+      if (!h.resident) sm = rank1_smem(h.L, false, f64, h.gj_smem);
+    }
+    smem_max = std::max(smem_max, sm);
+    h.out_off = out_off;
+    out_off += h.L + 1;
+    GridConst& q = c->gc[g];
+    q.L = h.L;
+    q.chains = h.chains;
+    q.item0 = h.item0;
+    q.resident = h.resident;
+    q.k = h.k;
+    q.n_wrap = h.n_wrap;
+    q.gj_smem = h.gj_smem;
+    q.lambda = h.lambda;
+    q.delta[0] = std::exp(-2.0 * h.lambda) - 1.0;
+    q.delta[1] = std::exp(2.0 * h.lambda) - 1.0;
+    q.dV[0] = std::exp(h.lambda) - 1.0;
+    q.dV[1] = std::exp(-h.lambda) - 1.0;
+    q.deltaf[0] = (float)q.delta[0];
+    q.deltaf[1] = (float)q.delta[1];
+    q.M = nullptr;
+  }
+
+  // device memory: one pool, grid-major per category
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o2 = off;
+    off += align256(bytes);
+    return o2;
+  };
+  std::vector<size_t> offM(n_grids), offG0(n_grids);
+  for (int g = 0; g < n_grids; ++g) {
+    offM[g] = take(sizeof(double) * (size_t)c->gh[g].L * c->gh[g].L);
+    offG0[g] = take(sizeof(double) * (size_t)c->gh[g].L);
+  }
+  struct ItemOff {
+    size_t s, G, ws, acc, bins, accD, cnt;
+  };
+  std::vector<ItemOff> io(c->n_items);
+  for (int g = 0; g < n_grids; ++g) {
+    const size_t L = c->gh[g].L;
+    for (int ch = 0; ch < c->gh[g].chains; ++ch) {
+      ItemOff& x = io[c->gh[g].item0 + ch];
+      x.G = take(2 * L * L * es);
+    }
+  }
+  // workspace, accumulators and counters after the matrices, grid-major
+  for (int i = 0; i < c->n_items; ++i) {
+    int g = 0;
+    while (g + 1 < n_grids && c->gh[g + 1].item0 <= i) ++g;
+    const size_t L = c->gh[g].L;
+    io[i].ws = take(sizeof(double) * 2 * L * L);
+  }
+  const size_t acc_begin = off;
+  std::vector<size_t> acc_grid_begin(n_grids + 1);
+  for (int g = 0; g < n_grids; ++g) {
+    acc_grid_begin[g] = off;
+    const size_t L = c->gh[g].L;
+    for (int ch = 0; ch < c->gh[g].chains; ++ch) {
+      ItemOff& x = io[c->gh[g].item0 + ch];
+      x.s = take(L);
+      x.acc = take(sizeof(double) * 2 * L);
+      x.bins = take(sizeof(double) * kBins * L);
+      x.accD = take(sizeof(double) * (1 + kBins));
+      x.cnt = take(sizeof(ChainCounters));
+    }
+  }
+  acc_grid_begin[n_grids] = off;
+  const size_t pool_bytes = off;
+  c->d_pool = (unsigned char*)dev_alloc(c, pool_bytes);
+  c->d_grids = (GridConst*)dev_alloc(c, sizeof(GridConst) * n_grids);
+  c->d_items = (ItemPtrs*)dev_alloc(c, sizeof(ItemPtrs) * c->n_items);
+  c->d_order = (int*)dev_alloc(c, sizeof(int) * c->n_items);
+  c->d_queue = (int*)dev_alloc(c, sizeof(int));
+  c->d_status = (int*)dev_alloc(c, sizeof(int));
+  c->d_account = (GridAccount*)dev_alloc(c, sizeof(GridAccount) * n_grids);
+  c->d_gout = (GridOut*)dev_alloc(c, sizeof(GridOut) * n_grids);
+  c->d_outG = (double*)dev_alloc(c, sizeof(double) * out_off);
+  c->d_outErr = (double*)dev_alloc(c, sizeof(double) * out_off);
+  c->d_out_off = (long long*)dev_alloc(c, sizeof(long long) * n_grids);
+  if (!c->d_pool || !c->d_grids || !c->d_items || !c->d_order || !c->d_queue || !c->d_status ||
+      !c->d_account || !c->d_gout || !c->d_outG || !c->d_outErr || !c->d_out_off)
+    return bail(fail(c, HFQMC_ENOMEM, "device allocation failed (" +
+                                          std::to_string(pool_bytes >> 20) + " MiB pool)"));
+  if ((e = cudaMallocHost(&c->h_gout, sizeof(GridOut) * n_grids)) != cudaSuccess ||
+      (e = cudaMallocHost(&c->h_status, sizeof(int))) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMallocHost"));
+  (void)acc_begin;
+
+  for (int g = 0; g < n_grids; ++g) c->gc[g].M = (const double*)(c->d_pool + offM[g]);
+  c->items.resize(c->n_items);
+  for (int g = 0; g < n_grids; ++g)
+    for (int ch = 0; ch < c->gh[g].chains; ++ch) {
+      const int i = c->gh[g].item0 + ch;
+      ItemPtrs& p = c->items[i];
+      p.grid = g;
+      p.chain = ch;
+      p.L = c->gh[g].L;
+      p.pad = 0;
+      p.s = (int8_t*)(c->d_pool + io[i].s);
+      p.G = (void*)(c->d_pool + io[i].G);
+      p.ws = (double*)(c->d_pool + io[i].ws);
+      p.acc = (double*)(c->d_pool + io[i].acc);
+      p.bins = (double*)(c->d_pool + io[i].bins);
+      p.accD = (double*)(c->d_pool + io[i].accD);
+      p.cnt = (ChainCounters*)(c->d_pool + io[i].cnt);
+    }
+  // longest-Lambda-first order (stable)
+  std::vector<int> order(c->n_items);
+  for (int i = 0; i < c->n_items; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return c->items[x].L > c->items[y].L; });
+  std::vector<long long> offs(n_grids);
+  for (int g = 0; g < n_grids; ++g) offs[g] = c->gh[g].out_off;
+
+  if ((e = cudaMemcpyAsync(c->d_grids, c->gc.data(), sizeof(GridConst) * n_grids, cudaMemcpyHostToDevice,
+                     c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
+  if ((e = cudaMemcpyAsync(c->d_items, c->items.data(), sizeof(ItemPtrs) * c->n_items,
+                     cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
+  if ((e = cudaMemcpyAsync(c->d_order, order.data(), sizeof(int) * c->n_items, cudaMemcpyHostToDevice,
+                     c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
+  if ((e = cudaMemcpyAsync(c->d_out_off, offs.data(), sizeof(long long) * n_grids,
+                     cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
+  if ((e = cudaMemsetAsync(c->d_pool + acc_grid_begin[0], 0, acc_grid_begin[n_grids] - acc_grid_begin[0],
+                     c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+  if ((e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+  if ((e = cudaMemsetAsync(c->d_account, 0, sizeof(GridAccount) * n_grids, c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+  if ((e = cudaMemsetAsync(c->d_gout, 0, sizeof(GridOut) * n_grids, c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+  for (int g = 0; g < n_grids; ++g) c->gh[g].out_off = offs[g];
+
+  // launch shape of the persistent sweep kernel
+  int threads = 0, occ = 0, r;
+  c->sweep_smem = smem_max;
+  if (o.precision == HFQMC_F32_DELAYED)
+    r = delayed_config(smem_max, &threads, &occ);
+  else
+    r = rank1_config(f64, smem_max, &threads, &occ);
+  if (r) return bail(cuda_fail(c, (cudaError_t)r, "sweep kernel configuration"));
+  if (occ < 1) return bail(fail(c, HFQMC_EINVAL, "sweep kernel does not fit on an SM"));
+  c->sweep_ctas = std::min(c->n_items, occ * c->n_sm);
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamSynchronize(create)"));
+  *out = c;
+  return HFQMC_OK;
+}
+
+int check_status(hfqmc_ctx* c) {
+  if (*c->h_status & kStatusSingular)
+    return fail(c, HFQMC_ENUMERIC, "zero pivot in an FP64 Gauss-Jordan recompute");
+  if (*c->h_status & kStatusNonFinite)
+    return fail(c, HFQMC_ENUMERIC, "non-finite Green matrix after a recompute");
+  if (*c->h_status & kStatusTimeout)
+    return fail(c, HFQMC_ETIMEOUT, "a bounded device wait gave up");
+  return HFQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hfqmc_default_opts(hfqmc_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HFQMC_F32_DELAYED;
+  o->k = 0;
+  o->n_wrap = 0;
+  o->accept_rule = HFQMC_METROPOLIS;
+  o->drift_warn = 1e-6;
+  o->drift_fail = 1e-3;
+  o->cuda_stream = nullptr;
+  o->autotune = 1;
+  o->flush = HFQMC_FLUSH_AUTO;
+  o->use_graph = 1;
+}
+
+int hfqmc_create(hfqmc_ctx** out, double beta, double U, const double* dtau, int n_grids,
+                 const int* chains_per_grid, uint64_t seed, const hfqmc_opts* opts) {
+  return create_impl(out, beta, &U, false, dtau, n_grids, chains_per_grid, seed, opts);
+}
+
+int hfqmc_create_ex(hfqmc_ctx** out, double beta, const double* U, const double* dtau,
+                    int n_grids, const int* chains_per_grid, uint64_t seed,
+                    const hfqmc_opts* opts) {
+  return create_impl(out, beta, U, true, dtau, n_grids, chains_per_grid, seed, opts);
+}
+
+int hfqmc_set_G0(hfqmc_ctx* c, int grid, const double* G0_tau) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids) return fail(c, HFQMC_EINVAL, "grid out of range");
+  if (!G0_tau) return fail(c, HFQMC_EINVAL, "G0_tau is NULL");
+  GridHost& h = c->gh[grid];
+  for (int k = 0; k < h.L; ++k)
+    if (!std::isfinite(G0_tau[k])) return fail(c, HFQMC_EINVAL, "G0_tau holds a non-finite value");
+  double* dM = const_cast<double*>(c->gc[grid].M);
+  double* dG0 = (double*)((unsigned char*)dM + align256(sizeof(double) * (size_t)h.L * h.L));
+  CK(cudaMemcpyAsync(dG0, G0_tau, sizeof(double) * h.L, cudaMemcpyHostToDevice, c->stream));
+  int r = launch_bath_matrix(h.L, dG0, dM, c->stream);
+  if (r) return cuda_fail(c, (cudaError_t)r, "bath matrix kernel");
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.grids = c->d_grids;
+  a.items = c->d_items;
+  a.status = c->d_status;
+  a.seed = c->seed;
+  r = launch_init_chains(a, c->d_grids + grid, h.item0, h.chains, h.L, f64_path(c), !h.ever_set,
+                         h.gj_smem != 0, c->stream);
+  if (r) return cuda_fail(c, (cudaError_t)r, "init kernel");
+  CK(cudaMemsetAsync(c->d_account + grid, 0, sizeof(GridAccount), c->stream));
+  CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  r = check_status(c);
+  if (r) return r;
+  h.g0_set = true;
+  h.ever_set = true;
+  return HFQMC_OK;
+}
+
+int hfqmc_sweep(hfqmc_ctx* c, int64_t n_warm, int64_t n_meas) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (n_warm < 0 || n_meas < 0) return fail(c, HFQMC_EINVAL, "negative sweep count");
+  if (n_warm + n_meas > (1ll << 31)) return fail(c, HFQMC_EINVAL, "too many sweeps in one call");
+  for (int g = 0; g < c->n_grids; ++g)
+    if (!c->gh[g].g0_set)
+      return fail(c, HFQMC_ESTATE, "hfqmc_set_G0 has not been called for grid " + std::to_string(g));
+  CK(cudaEventRecord(c->ev0, c->stream));
+  if (c->opts.use_graph) {
+    auto key = std::make_pair((long long)n_warm, (long long)n_meas);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      int r = enqueue_sweep(c, n_warm, n_meas);
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+      if (r) return r;
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+      cudaGraphExec_t ex;
+      cudaError_t e3 = cudaGraphInstantiate(&ex, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
+      it = c->graphs.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(it->second, c->stream));
+  } else {
+    int r = enqueue_sweep(c, n_warm, n_meas);
+    if (r) return r;
+  }
+  CK(cudaEventRecord(c->ev1, c->stream));
+  CK(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->last_ms = ms;
+  c->sweeps_done += n_warm + n_meas;
+  int r = check_status(c);
+  if (r) return r;
+  if (c->opts.drift_fail > 0.0)
+    for (int g = 0; g < c->n_grids; ++g)
+      if (c->h_gout[g].drift > c->opts.drift_fail) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "drift %.3e exceeds drift_fail %.3e on grid %d",
+                      c->h_gout[g].drift, c->opts.drift_fail, g);
+        return fail(c, HFQMC_EDRIFT, buf);
+      }
+  return HFQMC_OK;
+}
+
+int hfqmc_get_G(hfqmc_ctx* c, int grid, double* G_tau, double* G_err) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids) return fail(c, HFQMC_EINVAL, "grid out of range");
+  if (!G_tau) return fail(c, HFQMC_EINVAL, "G_tau is NULL");
+  const GridHost& h = c->gh[grid];
+  if (!h.g0_set) return fail(c, HFQMC_ESTATE, "no G0 set for this grid");
+  CK(cudaMemcpyAsync(G_tau, c->d_outG + h.out_off, sizeof(double) * (h.L + 1),
+                     cudaMemcpyDeviceToHost, c->stream));
+  if (G_err)
+    CK(cudaMemcpyAsync(G_err, c->d_outErr + h.out_off, sizeof(double) * (h.L + 1),
+                       cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HFQMC_OK;
+}
+
+int hfqmc_get_D(hfqmc_ctx* c, int grid, double* D, double* D_err) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids) return fail(c, HFQMC_EINVAL, "grid out of range");
+  GridOut o;
+  CK(cudaMemcpyAsync(&o, c->d_gout + grid, sizeof(GridOut), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (D) *D = o.D;
+  if (D_err) *D_err = o.D_err;
+  return HFQMC_OK;
+}
+
+int hfqmc_get_stats(hfqmc_ctx* c, int grid, hfqmc_stats* out) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids || !out) return fail(c, HFQMC_EINVAL, "bad argument");
+  GridOut o;
+  CK(cudaMemcpyAsync(&o, c->d_gout + grid, sizeof(GridOut), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const GridHost& h = c->gh[grid];
+  out->L = h.L;
+  out->chains = h.chains;
+  out->k = h.k;
+  out->n_wrap = h.n_wrap;
+  out->sweeps = c->sweeps_done;
+  out->proposals = o.proposals;
+  out->accepted = o.accepted;
+  out->recomputes = o.recomputes;
+  out->numeric_errors = o.bad;
+  out->accept_rate = o.proposals ? (double)o.accepted / (double)o.proposals : 0.0;
+  out->drift_max = o.drift;
+  out->last_sweep_ms = c->last_ms;
+  return HFQMC_OK;
+}
+
+int hfqmc_grid_size(hfqmc_ctx* c, int grid, int* L) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids || !L) return fail(c, HFQMC_EINVAL, "bad argument");
+  *L = c->gh[grid].L;
+  return HFQMC_OK;
+}
+
+int hfqmc_get_chain(hfqmc_ctx* c, int grid, int chain, int8_t* s, double* G_up, double* G_dn,
+                    int64_t* counters, double* acc) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids) return fail(c, HFQMC_EINVAL, "grid out of range");
+  const GridHost& h = c->gh[grid];
+  if (chain < 0 || chain >= h.chains) return fail(c, HFQMC_EINVAL, "chain out of range");
+  const ItemPtrs& p = c->items[h.item0 + chain];
+  const size_t L = h.L, LL = L * L;
+  if (s) CK(cudaMemcpyAsync(s, p.s, L, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<float> tmp;
+  if (G_up || G_dn) {
+    if (f64_path(c)) {
+      if (G_up) CK(cudaMemcpyAsync(G_up, p.G, LL * 8, cudaMemcpyDeviceToHost, c->stream));
+      if (G_dn)
+        CK(cudaMemcpyAsync(G_dn, (double*)p.G + LL, LL * 8, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      tmp.resize(2 * LL);
+      CK(cudaMemcpyAsync(tmp.data(), p.G, 2 * LL * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  ChainCounters cc;
+  CK(cudaMemcpyAsync(&cc, p.cnt, sizeof(cc), cudaMemcpyDeviceToHost, c->stream));
+  if (acc) CK(cudaMemcpyAsync(acc, p.acc, 2 * L * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (!tmp.empty()) {
+    if (G_up)
+      for (size_t e = 0; e < LL; ++e) G_up[e] = tmp[e];
+    if (G_dn)
+      for (size_t e = 0; e < LL; ++e) G_dn[e] = tmp[LL + e];
+  }
+  if (counters) {
+    counters[0] = cc.proposals;
+    counters[1] = cc.accepted;
+    counters[2] = cc.recomputes;
+    counters[3] = (int64_t)cc.hash;
+    counters[4] = cc.bad;
+    counters[5] = cc.t;
+  }
+  return HFQMC_OK;
+}
+
+const char* hfqmc_last_error(const hfqmc_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+void hfqmc_destroy(hfqmc_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* p : c->allocs) {
+    if (c->opts.alloc && c->opts.free)
+      c->opts.free(p, c->opts.alloc_user);
+    else if (!c->opts.alloc)
+      cudaFree(p);
+  }
+  if (c->h_gout) cudaFreeHost(c->h_gout);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Set-up and reduction kernels of the sweep library:
+//  * bath matrix M of a grid from its G0(tau_k) samples (antiperiodic Toeplitz);
+//  * per-chain initial field (Philox) and FP64 Gauss-Jordan Green matrices;
+//  * per-call measured-sweep bookkeeping;
+//  * per-grid mean over chains and error bars ("the raw Green functions are
+//    averaged over 10-20 impurity solutions", "Multigrid HF-QMC method" section).
+#include "hfq_device.cuh"
+#include "hfq_gj.cuh"
+#include "hfq_launch.h"
+
+namespace hfq {
+
+__global__ void k_bath_matrix(int L, const double* __restrict__ G0, double* __restrict__ M) {
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < L; j += blockDim.x)
+    M[(size_t)i * L + j] = (i >= j) ? -G0[i - j] : G0[i - j + L];
+}
+
+int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st) {
+  k_bath_matrix<<<L, 128, 0, st>>>(L, G0_tau, M);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridConst* gptr, int item0,
+                                                     int first_time) {
+  constexpr int NT = 256;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double red[NT / 32];
+  __shared__ int redi[NT / 32];
+  __shared__ double s_inv;
+  __shared__ int s_piv;
+  const int tid = threadIdx.x;
+  const ItemPtrs ip = a.items[item0 + blockIdx.x];
+  const GridConst gc = *gptr;
+  const int L = gc.L;
+  double* colk = reinterpret_cast<double*>(dsm);
+  double* W = gc.gj_smem ? colk + L : ip.ws;
+  if (first_time)
+    for (int l = tid; l < L; l += NT) ip.s[l] = initial_spin(l, ip.chain, ip.grid, a.seed);
+  __syncthreads();
+  T* G = reinterpret_cast<T*>(ip.G);
+  recompute_green<T, NT>(gc, ip.s, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk,
+                         false, a.status);
+  for (int k = tid; k < 2 * L; k += NT) ip.acc[k] = 0.0;
+  for (int k = tid; k < kBins * L; k += NT) ip.bins[k] = 0.0;
+  for (int k = tid; k < 1 + kBins; k += NT) ip.accD[k] = 0.0;
+  if (tid == 0) {
+    ChainCounters c;
+    if (first_time) {
+      c.t = 0;
+      c.proposals = 0;
+      c.accepted = 0;
+      c.recomputes = 0;
+      c.hash = kFnvOffset;
+      c.bad = 0;
+      c.status = 0;
+      c.pad = 0;
+    } else {
+      c = *ip.cnt;
+    }
+    c.drift = 0.0;
+    *ip.cnt = c;
+  }
+}
+
+size_t init_smem(int L, bool gj_smem) {
+  return (size_t)L * sizeof(double) + (gj_smem ? gj_smem_bytes(L) : 0);
+}
+
+int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item0, int n_chains,
+                       int L, bool f64, bool first_time, bool gj_smem, cudaStream_t st) {
+  const size_t sm = init_smem(L, gj_smem);
+  cudaError_t e;
+  if (f64) {
+    e = cudaFuncSetAttribute(k_init_chains<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    k_init_chains<double><<<n_chains, 256, sm, st>>>(a, d_grid_ptr, item0, first_time ? 1 : 0);
+  } else {
+    e = cudaFuncSetAttribute(k_init_chains<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    k_init_chains<float><<<n_chains, 256, sm, st>>>(a, d_grid_ptr, item0, first_time ? 1 : 0);
+  }
+  return (int)cudaGetLastError();
+}
+
+// Measured sweep m (0-based within one call of n_meas) goes to bin floor(32 m / n_meas);
+// bin b therefore receives ceil((b+1) n / 32) - ceil(b n / 32) sweeps.
+__global__ void k_account(GridAccount* acc, int n_grids, long long n_meas) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_grids || n_meas <= 0) return;
+  acc[g].n_meas += n_meas;
+  for (int b = 0; b < kBins; ++b) {
+    const long long lo = ((long long)b * n_meas + kBins - 1) / kBins;
+    const long long hi = ((long long)(b + 1) * n_meas + kBins - 1) / kBins;
+    acc[g].bin_count[b] += hi - lo;
+  }
+}
+
+int launch_account(GridAccount* acc, int n_grids, long long n_meas, cudaStream_t st) {
+  k_account<<<(n_grids + 127) / 128, 128, 0, st>>>(acc, n_grids, n_meas);
+  return (int)cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_reduce(const GridConst* grids, const ItemPtrs* items,
+                                                const GridAccount* acc, GridOut* gout,
+                                                double* outG, double* outErr,
+                                                const long long* out_off) {
+  const int g = blockIdx.x, tid = threadIdx.x;
+  const GridConst gc = grids[g];
+  const int L = gc.L, nc = gc.chains, i0 = gc.item0;
+  const GridAccount& A = acc[g];
+  const double N = (double)A.n_meas;
+  double* oG = outG + out_off[g];
+  double* oE = outErr + out_off[g];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  for (int k = tid; k < L; k += blockDim.x) {
+    double mean = nan, err = nan;
+    if (A.n_meas > 0) {
+      if (nc >= 2) {
+        double s = 0.0;
+        for (int c = 0; c < nc; ++c) {
+          const double* ac = items[i0 + c].acc;
+          s += -(ac[k] + ac[L + k]) / (2.0 * N);
+        }
+        mean = s / nc;
+        double v = 0.0;
+        for (int c = 0; c < nc; ++c) {
+          const double* ac = items[i0 + c].acc;
+          const double d = -(ac[k] + ac[L + k]) / (2.0 * N) - mean;
+          v += d * d;
+        }
+        err = sqrt(v / (nc - 1) / nc);
+      } else {
+        const ItemPtrs ip = items[i0];
+        mean = -(ip.acc[k] + ip.acc[L + k]) / (2.0 * N);
+        int nb = 0;
+        double s = 0.0;
+        for (int b = 0; b < kBins; ++b)
+          if (A.bin_count[b] > 0) {
+            s += -ip.bins[(size_t)b * L + k] / (double)A.bin_count[b];
+            ++nb;
+          }
+        if (nb >= 2) {
+          const double bm = s / nb;
+          double v = 0.0;
+          for (int b = 0; b < kBins; ++b)
+            if (A.bin_count[b] > 0) {
+              const double d = -ip.bins[(size_t)b * L + k] / (double)A.bin_count[b] - bm;
+              v += d * d;
+            }
+          err = sqrt(v / (nb - 1) / nb);
+        }
+      }
+    }
+    oG[k] = mean;
+    oE[k] = err;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    oG[L] = -1.0 - oG[0];
+    oE[L] = oE[0];
+    GridOut o;
+    o.proposals = o.accepted = o.recomputes = o.bad = 0;
+    o.drift = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const ChainCounters cc = *items[i0 + c].cnt;
+      o.proposals += cc.proposals;
+      o.accepted += cc.accepted;
+      o.recomputes += cc.recomputes;
+      o.bad += cc.bad;
+      o.drift = fmax(o.drift, cc.drift);
+    }
+    o.D = nan;
+    o.D_err = nan;
+    if (A.n_meas > 0) {
+      if (nc >= 2) {
+        double s = 0.0, v = 0.0;
+        for (int c = 0; c < nc; ++c) s += items[i0 + c].accD[0] / N;
+        const double m = s / nc;
+        for (int c = 0; c < nc; ++c) {
+          const double d = items[i0 + c].accD[0] / N - m;
+          v += d * d;
+        }
+        o.D = m;
+        o.D_err = sqrt(v / (nc - 1) / nc);
+      } else {
+        o.D = items[i0].accD[0] / N;
+        int nb = 0;
+        double s = 0.0, v = 0.0;
+        for (int b = 0; b < kBins; ++b)
+          if (A.bin_count[b] > 0) {
+            s += items[i0].accD[1 + b] / (double)A.bin_count[b];
+            ++nb;
+          }
+        if (nb >= 2) {
+          const double m = s / nb;
+          for (int b = 0; b < kBins; ++b)
+            if (A.bin_count[b] > 0) {
+              const double d = items[i0].accD[1 + b] / (double)A.bin_count[b] - m;
+              v += d * d;
+            }
+          o.D_err = sqrt(v / (nb - 1) / nb);
+        }
+      }
+    }
+    o.pad = 0.0;
+    gout[g] = o;
+  }
+}
+
+int launch_reduce(const GridConst* grids, const ItemPtrs* items, const GridAccount* acc,
+                  GridOut* gout, double* outG, double* outErr, const long long* out_off,
+                  int n_grids, cudaStream_t st) {
+  k_reduce<<<n_grids, 256, 0, st>>>(grids, items, acc, gout, outG, outErr, out_off);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace hfq

@@ -1,0 +1,115 @@
+"""FP32 paths (rank-1 and delayed rank-k with tcgen05 or FFMA flush) against
+the FP64 oracle and the FP64 GPU path, through the C ABI.
+
+The FP32 paths round the flip ratio to FP32, so they cannot be held to
+decision parity forever; over short runs they follow the same accept/reject
+sequence (identical decision hash) as the FP64 oracle, and their Green
+matrices stay within the FP32 drift of it.  The measured G(tau) must agree
+with an FP64 run of the same chains within 1e-5 on top of the statistical
+error."""
+import numpy as np
+import pytest
+
+from gpu_common import lib, make_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,flush,k", [
+    ("f32_rank1", "auto", 0),
+    ("f32_delayed", "ffma", 8),
+    ("f32_delayed", "tcgen05", 16),
+    ("f32_delayed", "tcgen05", 8),
+])
+def test_short_runs_follow_fp64_decisions(orc, precision, flush, k):
+    ctx, q = make_pair(orc, 20.0, [(5.0, 0.2)], [6], precision=precision, n_wrap=-1, flush=flush,
+                       k=k, drift_fail=1.0)
+    ctx.sweep(2, 0)
+    q.sweep(2, 0)
+    same = 0
+    for c, och in enumerate(q.chains[0]):
+        gc = ctx.get_chain(0, c)
+        if gc["hash"] == och.decision_hash:
+            same += 1
+            assert np.array_equal(gc["s"], och.s)
+            err = max(np.abs(gc["Gup"] - och.Gup).max(), np.abs(gc["Gdn"] - och.Gdn).max())
+            assert err < 1e-3, err
+    assert same >= 5
+
+
+def test_uneven_grids_delayed_with_recompute(orc):
+    # ragged Lambda, shared-memory and HBM-resident G, shared-memory and HBM recompute
+    grids = [(4.0, 10.0 / 37), (5.0, 0.1), (5.2, 10.0 / 130)]
+    ctx, q = make_pair(orc, 10.0, grids, [3, 2, 2], precision="f32_delayed", n_wrap=32,
+                       drift_fail=1.0)
+    ctx.sweep(1, 1)
+    q.sweep(1, 1)
+    for g in range(3):
+        st = ctx.get_stats(g)
+        assert st["recomputes"] > 0
+        assert st["drift_max"] < 1e-3
+        for c, och in enumerate(q.chains[g]):
+            gc = ctx.get_chain(g, c)
+            if gc["hash"] == och.decision_hash:
+                err = max(np.abs(gc["Gup"] - och.Gup).max(), np.abs(gc["Gdn"] - och.Gdn).max())
+                # right after an FP64 recompute the matrices agree to FP32 rounding
+                assert err < 1e-3
+
+
+def test_tcgen05_flush_matches_ffma_flush():
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    out = {}
+    for flush in ("ffma", "tcgen05"):
+        ctx = h.HFQMC(40.0, 5.0, [40.0 / 160, 40.0 / 240], [2, 2], seed=3, precision="f32_delayed",
+                      k=16, n_wrap=-1, flush=flush, drift_fail=1.0)
+        ctx.set_G0(0, inputs.bethe_G0_tau(40.0, 160))
+        ctx.set_G0(1, inputs.bethe_G0_tau(40.0, 240))
+        ctx.sweep(1, 0)
+        out[flush] = [ctx.get_chain(g, c) for g in range(2) for c in range(2)]
+        ctx.close()
+    for a, b in zip(out["ffma"], out["tcgen05"]):
+        if a["hash"] == b["hash"]:
+            assert np.max(np.abs(a["Gup"] - b["Gup"])) < 1e-3
+            assert np.max(np.abs(a["Gdn"] - b["Gdn"])) < 1e-3
+
+
+def test_G_tau_fp32_within_1e5_of_fp64():
+    """Same chains, same Philox stream: FP32 delayed vs FP64 rank-1 measured
+    G(tau) must differ by at most 1e-5 + 3 sigma (sigma of the difference)."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    beta, U, L, nc = 20.0, 5.0, 100, 64
+    g0 = inputs.bethe_G0_tau(beta, L)
+    res = {}
+    for prec in ("f64_rank1", "f32_delayed"):
+        ctx = h.HFQMC(beta, U, [beta / L], [nc], seed=11, precision=prec, n_wrap=256,
+                      drift_fail=1.0)
+        ctx.set_G0(0, g0)
+        ctx.sweep(20, 200)
+        res[prec] = ctx.get_G(0)
+        ctx.close()
+    G64, E64 = res["f64_rank1"]
+    G32, E32 = res["f32_delayed"]
+    sig = np.sqrt(E64 ** 2 + E32 ** 2)
+    assert np.all(np.abs(G32 - G64) <= 1e-5 + 3 * sig), np.max(np.abs(G32 - G64) / sig)
+
+
+def test_drift_is_reported_and_bounded():
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    ctx = h.HFQMC(20.0, 5.0, [0.2], [16], precision="f32_delayed", n_wrap=64, drift_fail=1e-2)
+    ctx.set_G0(0, inputs.bethe_G0_tau(20.0, 100))
+    ctx.sweep(5, 20)
+    st = ctx.get_stats(0)
+    assert st["recomputes"] > 0 and 0.0 < st["drift_max"] < 1e-2
+
+
+def test_drift_fail_threshold_raises():
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    ctx = h.HFQMC(20.0, 5.0, [0.2], [4], precision="f32_delayed", n_wrap=64, drift_fail=1e-12)
+    ctx.set_G0(0, inputs.bethe_G0_tau(20.0, 100))
+    with pytest.raises(h.HFQMCError) as ei:
+        ctx.sweep(5, 5)
+    assert ei.value.name == "EDRIFT"
