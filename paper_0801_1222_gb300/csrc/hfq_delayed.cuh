@@ -40,7 +40,7 @@ __host__ __device__ inline size_t del_stage_bytes(int K) {
 __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem) {
   DelLayout d;
   d.ldS = L | 1;
-  d.KP = K + 1;  // odd pitch: a warp reading 32 rows hits 32 banks
+  d.KP = K + 4;  // 16-byte rows; (K+4) mod 32 spreads 8 rows of a 16-byte load over all banks
   d.K8 = (K + 7) / 8 * 8;
   size_t o = 0;
   d.off_colk = o;
@@ -68,10 +68,10 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   return d;
 }
 
-__device__ __forceinline__ bool del_decide(const GridConst& gc, float gu, float gd, int sl, float u,
+__device__ __forceinline__ bool del_decide(float d0, float d1, float gu, float gd, int sl, float u,
                                            int rule, bool* bad) {
-  const float du = sl > 0 ? gc.deltaf[0] : gc.deltaf[1];
-  const float dd = sl > 0 ? gc.deltaf[1] : gc.deltaf[0];
+  const float du = sl > 0 ? d0 : d1;
+  const float dd = sl > 0 ? d1 : d0;
   const float Ru = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gu), du));
   const float Rd = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gd), dd));
   const float R = __fmul_rn(Ru, Rd);
@@ -79,10 +79,10 @@ __device__ __forceinline__ bool del_decide(const GridConst& gc, float gu, float 
   return rule == 0 ? (u < R) : (__fmul_rn(u, __fadd_rn(1.f, R)) < R);
 }
 
-__device__ __forceinline__ void del_factors(const GridConst& gc, float gu, float gd, int sl, float* fu,
+__device__ __forceinline__ void del_factors(float d0, float d1, float gu, float gd, int sl, float* fu,
                                             float* fd) {
-  const float du = sl > 0 ? gc.deltaf[0] : gc.deltaf[1];
-  const float dd = sl > 0 ? gc.deltaf[1] : gc.deltaf[0];
+  const float du = sl > 0 ? d0 : d1;
+  const float dd = sl > 0 ? d1 : d0;
   const float Ru = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gu), du));
   const float Rd = __fadd_rn(1.f, __fmul_rn(__fsub_rn(1.f, gd), dd));
   *fu = du / Ru;

@@ -5,10 +5,11 @@
 // followed by the drift check max |G_fast - G_fresh|.
 //
 // Algorithm: Gauss-Jordan elimination with partial pivoting on the augmented
-// L x 2L matrix [A | M] held in the chain's HBM workspace (L2-resident for
-// the sizes used).  One CTA; per pivot column three barriers (pivot search,
-// row swap + scale, elimination).  Cost 1.5 L^3 DFMA per spin, bound by the
-// FP64 pipe (about 2 DFMA/clk/SM on GB300).
+// L x 2L matrix [A | M], in shared memory when it fits (Lambda <= 118) and in
+// the chain's HBM workspace otherwise (L2-resident for the sizes used).  One
+// CTA; per pivot column three barriers (pivot search, row swap + scale,
+// elimination).  Cost 1.5 L^3 DFMA per spin, bound by the FP64 pipe (about
+// 2 DFMA/clk/SM on GB300).
 #pragma once
 #include "hfq_device.cuh"
 
@@ -93,22 +94,38 @@ __device__ int gj_eliminate(double* W, int L, double* red, int* redi, double* s_
         const int j = c0 + lane + 32 * c;
         rk[c] = j < ld ? wk[j] : 0.0;
       }
-      for (int i = warp; i < L; i += NW) {
-        if (i == k) continue;
+      // rows warp, warp+NW, ...: the loads of the next row are issued before
+      // the stores of the current one, so two rows are in flight per warp
+      double v[kGjChunk];
+      int i = warp;
+      if (i < L) {
+#pragma unroll
+        for (int c = 0; c < kGjChunk; ++c) {
+          const int j = c0 + lane + 32 * c;
+          v[c] = j < ld ? W[(size_t)i * ld + j] : 0.0;
+        }
+      }
+      for (; i < L; i += NW) {
+        const int inext = i + NW;
+        double vn[kGjChunk];
+        if (inext < L) {
+#pragma unroll
+          for (int c = 0; c < kGjChunk; ++c) {
+            const int j = c0 + lane + 32 * c;
+            vn[c] = j < ld ? W[(size_t)inext * ld + j] : 0.0;
+          }
+        }
         const double f = colk[i];
-        if (f == 0.0) continue;
-        double* wi = W + (size_t)i * ld;
-        double v[kGjChunk];
+        if (i != k && f != 0.0) {
+          double* wi = W + (size_t)i * ld;
 #pragma unroll
-        for (int c = 0; c < kGjChunk; ++c) {
-          const int j = c0 + lane + 32 * c;
-          v[c] = j < ld ? wi[j] : 0.0;
+          for (int c = 0; c < kGjChunk; ++c) {
+            const int j = c0 + lane + 32 * c;
+            if (j < ld) wi[j] = fma(-f, rk[c], v[c]);
+          }
         }
 #pragma unroll
-        for (int c = 0; c < kGjChunk; ++c) {
-          const int j = c0 + lane + 32 * c;
-          if (j < ld) wi[j] = fma(-f, rk[c], v[c]);
-        }
+        for (int c = 0; c < kGjChunk; ++c) v[c] = vn[c];
       }
     }
     __syncthreads();

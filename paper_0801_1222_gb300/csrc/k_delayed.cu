@@ -70,6 +70,8 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
     int8_t* ss = reinterpret_cast<int8_t*>(smem + lay.off_s);
     unsigned char* stage = smem + lay.off_stage;
     const int KP = lay.KP;
+    const float d0 = gc.deltaf[0], d1 = gc.deltaf[1];
+    const int rule = a.accept_rule;
 
     if (resident) {
       for (int i = warp; i < 2 * L; i += NW)
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
         for (int w = l0; w < L; w += 32) {
           const int l = w + lane;
           bool acc = false, bad = false;
-          if (l < L) acc = del_decide(gc, diag[l], diag[L + l], ss[l], us[l], a.accept_rule, &bad);
+          if (l < L) acc = del_decide(d0, d1, diag[l], diag[L + l], ss[l], us[l], rule, &bad);
           const unsigned b = __ballot_sync(0xffffffffu, acc);
           const unsigned bb = __ballot_sync(0xffffffffu, bad);
           if (b) {
@@ -134,24 +136,45 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
         const int l = first;
         const int sl = ss[l];
         float fu, fd;
-        del_factors(gc, diag[l], diag[L + l], sl, &fu, &fd);
-        // append column j of the panels: item (sp, i) -> u_i, w_i and the diagonal
+        del_factors(d0, d1, diag[l], diag[L + l], sl, &fu, &fd);
+        // append column j of the panels: item (sp, i) -> u_i, w_i and the diagonal.
+        // Current column / row entries are the base G entry plus a length-j dot
+        // product with the panels (16-byte loads, four partial sums).
         for (int it = tid; it < 2 * L; it += NT) {
           const int sp = it >= L;
           const int i = it - sp * L;
           const float* G = sp ? Gd : Gu;
           float* U = Pu + (size_t)sp * L * KP;
           float* W = Pw + (size_t)sp * L * KP;
-          float cc = G[(size_t)i * ld + l];
-          float rr = G[(size_t)l * ld + i];
-          const float* Ui = U + (size_t)i * KP;
-          const float* Ul = U + (size_t)l * KP;
-          const float* Wi = W + (size_t)i * KP;
-          const float* Wl = W + (size_t)l * KP;
-          for (int m = 0; m < j; ++m) {
-            cc = __fmaf_rn(Ui[m], Wl[m], cc);
-            rr = __fmaf_rn(Ul[m], Wi[m], rr);
+          const float g_il = G[(size_t)i * ld + l];
+          const float g_li = G[(size_t)l * ld + i];
+          const float4* Ui = reinterpret_cast<const float4*>(U + (size_t)i * KP);
+          const float4* Ul = reinterpret_cast<const float4*>(U + (size_t)l * KP);
+          const float4* Wi = reinterpret_cast<const float4*>(W + (size_t)i * KP);
+          const float4* Wl = reinterpret_cast<const float4*>(W + (size_t)l * KP);
+          float c4[4] = {0.f, 0.f, 0.f, 0.f}, r4[4] = {0.f, 0.f, 0.f, 0.f};
+          const int j4 = j >> 2;
+          for (int q = 0; q < j4; ++q) {
+            const float4 ui = Ui[q], wl = Wl[q], ul = Ul[q], wi = Wi[q];
+            c4[0] = __fmaf_rn(ui.x, wl.x, c4[0]);
+            c4[1] = __fmaf_rn(ui.y, wl.y, c4[1]);
+            c4[2] = __fmaf_rn(ui.z, wl.z, c4[2]);
+            c4[3] = __fmaf_rn(ui.w, wl.w, c4[3]);
+            r4[0] = __fmaf_rn(ul.x, wi.x, r4[0]);
+            r4[1] = __fmaf_rn(ul.y, wi.y, r4[1]);
+            r4[2] = __fmaf_rn(ul.z, wi.z, r4[2]);
+            r4[3] = __fmaf_rn(ul.w, wi.w, r4[3]);
           }
+          const float* Uis = U + (size_t)i * KP;
+          const float* Uls = U + (size_t)l * KP;
+          const float* Wis = W + (size_t)i * KP;
+          const float* Wls = W + (size_t)l * KP;
+          for (int m = 4 * j4; m < j; ++m) {
+            c4[0] = __fmaf_rn(Uis[m], Wls[m], c4[0]);
+            r4[0] = __fmaf_rn(Uls[m], Wis[m], r4[0]);
+          }
+          const float cc = g_il + ((c4[0] + c4[1]) + (c4[2] + c4[3]));
+          const float rr = g_li + ((r4[0] + r4[1]) + (r4[2] + r4[3]));
           const float uu = cc - (i == l ? 1.f : 0.f);
           const float ww = rr * (sp ? fd : fu);
           U[(size_t)i * KP + j] = uu;
