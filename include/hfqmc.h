@@ -174,6 +174,42 @@ int hfqmc_grid_size(hfqmc_ctx *ctx, int grid, int *L);
 int hfqmc_get_chain(hfqmc_ctx *ctx, int grid, int chain, int8_t *s, double *G_up,
                     double *G_dn, int64_t *counters, double *acc);
 
+/* ---- entry point that allocates nothing --------------------------------
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory themselves or through this library -- a host
+ * runtime that hands out every device buffer from its own pool, a plugin
+ * barred from the CUDA allocator, code running where cudaMalloc is not
+ * allowed.  It computes what hfqmc_set_G0 computes for each chain: for one
+ * HS field s the FP64 Green matrices of both spins,
+ *   G^sigma = [1 + (1 - M)(e^{sigma lambda s} - 1)]^{-1} M,
+ *   cosh(lambda) = exp(dtau U / 2), sigma = +1 (G_up), -1 (G_dn),
+ * with M the antiperiodic bath matrix built from G0_tau as in hfqmc_set_G0,
+ * by Gauss-Jordan elimination with partial pivoting.
+ *
+ * Arguments (all pointers are DEVICE memory owned by the caller):
+ *   G0_tau  L doubles, G0(k dtau), k = 0..L-1, physical sign, G0_tau[0] = G0(0+)
+ *   s       L int8 values, each +1 or -1
+ *   G_up, G_dn  L x L doubles each, row-major, written
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream)
+ *   status_out   optional host int: the device status bits of this call
+ * 1 <= L <= HFQMC_NOALLOC_MAX_L; larger L returns HFQMC_EINVAL before any
+ * device work.  The call returns after its work on cuda_stream is done:
+ * HFQMC_OK, HFQMC_ENUMERIC (zero pivot or non-finite G), HFQMC_ECUDA.
+ *
+ * Memory: the bath matrix and the [A | M] workspace live in one file-scope
+ * device array of 3 * HFQMC_NOALLOC_MAX_L^2 doubles (1.5 MiB) that every GPU
+ * which loads the library holds until the process exits.  The call allocates
+ * nothing (no cudaMalloc, no allocating library routine).  The first call on
+ * a device looks up the array's device address once, with that device
+ * current, so that first call should come before any stream capture.  Every
+ * call uses the same array and leaves its contents behind (each call
+ * overwrites what it reads); calls that overlap on the GPU -- from several
+ * streams or threads at once -- race on it and must be serialised by the
+ * caller. */
+#define HFQMC_NOALLOC_MAX_L 256
+int hfqmc_green_noalloc(const double *G0_tau, const int8_t *s, int L, double dtau, double U,
+                        double *G_up, double *G_dn, void *cuda_stream, int *status_out);
+
 /* Message of the last failed call on ctx (or of the last failed create when ctx is NULL). */
 const char *hfqmc_last_error(const hfqmc_ctx *ctx);
 

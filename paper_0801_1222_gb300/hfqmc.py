@@ -93,8 +93,10 @@ def load():
     lib.hfqmc_last_error.restype = ctypes.c_char_p
     lib.hfqmc_destroy.argtypes = [P]
     lib.hfqmc_destroy.restype = None
+    lib.hfqmc_green_noalloc.argtypes = [P, P, I, D, D, P, P, P, ctypes.POINTER(I)]
     for name in ("hfqmc_create", "hfqmc_create_ex", "hfqmc_set_G0", "hfqmc_sweep", "hfqmc_get_G",
-                 "hfqmc_get_D", "hfqmc_get_stats", "hfqmc_grid_size", "hfqmc_get_chain"):
+                 "hfqmc_get_D", "hfqmc_get_stats", "hfqmc_grid_size", "hfqmc_get_chain",
+                 "hfqmc_green_noalloc"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -184,6 +186,23 @@ def hfqmc_get_chain(ctx, grid, chain) -> dict:
     return dict(s=s, Gup=Gu, Gdn=Gd, proposals=int(cnt[0]), accepted=int(cnt[1]),
                 recomputes=int(cnt[2]), hash=int(np.array(cnt[3]).view(np.uint64)),
                 bad=int(cnt[4]), t=int(cnt[5]), acc=acc)
+
+
+NOALLOC_MAX_L = 256
+
+
+def hfqmc_green_noalloc(G0_tau_dev: int, s_dev: int, L: int, dtau: float, U: float, G_up_dev: int,
+                        G_dn_dev: int, stream: int = 0) -> int:
+    """FP64 G^up, G^dn of one field from caller-owned device buffers (integer
+    device addresses), without any device allocation; returns the status bits."""
+    st = ctypes.c_int(0)
+    rc = load().hfqmc_green_noalloc(ctypes.c_void_p(G0_tau_dev), ctypes.c_void_p(s_dev), int(L),
+                                    float(dtau), float(U), ctypes.c_void_p(G_up_dev),
+                                    ctypes.c_void_p(G_dn_dev), ctypes.c_void_p(stream),
+                                    ctypes.byref(st))
+    if rc != HFQMC_OK:
+        raise HFQMCError(rc, f"hfqmc_green_noalloc (L={L}, status bits {st.value})")
+    return st.value
 
 
 def hfqmc_last_error(ctx) -> str:
