@@ -264,6 +264,11 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     // the FP64 recompute works in shared memory when [A | M] fits next to the head
     h.gj_smem = o.gj_smem >= 0 && gj_smem_bytes(h.L) + 4 * (size_t)h.L * 8 + 1024 <= kSmemMax;
     if (o.precision == HFQMC_F32_DELAYED) {
+      if (h.L > 512) {
+        g_create_error = "the delayed path handles Lambda <= 512 (two rows per thread)";
+        hfqmc_destroy(c);
+        return HFQMC_EINVAL;
+      }
       // the panels of both spins must fit in shared memory: lower k if needed
       while (h.k > 8 && delayed_smem(h.L, h.k, false, h.gj_smem) > kSmemMax) h.k -= 8;
       if (delayed_smem(h.L, h.k, false, h.gj_smem) > kSmemMax) {

@@ -4,16 +4,24 @@
 // The accepted flips of a chain are not applied one by one.  After j accepted
 // flips since the last flush the current Green matrix is
 //     G_cur = G + U W^T,   U, W: L x j panels (per spin),
-// so a proposal needs only the current diagonal (kept incrementally), and an
-// accepted flip at slice l appends
+// and an accepted flip at slice l appends
 //     u = G_cur[:, l] - e_l,           w = (Delta / R) G_cur[l, :],
-// whose entries cost O(j) each (the base column / row plus a length-j dot
-// product with the panels).  Every k accepted flips the panels are flushed,
-// G += U W^T -- a dense L x L x k contraction per spin (tcgen05 tensor cores
-// with split TF32, or FP32 FMA).  The rank-1 formula of the Hirsch-Fye update
-// is recovered exactly in exact arithmetic; only the rounding differs.
+// whose entries cost O(j) each (the base column / row entry plus a length-j
+// dot product with the panels).  Every k accepted flips the panels are
+// flushed, G += U W^T -- a dense L x L x k contraction per spin (tcgen05
+// tensor cores with split TF32, or FP32 FMA).  In exact arithmetic this is
+// the Hirsch-Fye rank-1 update applied k times; only the rounding differs.
 // The panels are also flushed before every measurement and every FP64
 // recompute (every n_wrap accepted flips).
+//
+// Work split: thread t owns spin (t & 1) of rows r = t/2 + 128 q.  For its
+// rows it appends the panel entries, keeps the current diagonal G_cur[r][r]
+// in registers, swaps it with its partner thread (the other spin) by one
+// shuffle, and right away evaluates slice r as the next proposal (flip ratio
+// from the new diagonals, Philox uniform drawn at the start of the sweep).
+// Rejections change nothing, so the next accepted slice is the lowest r > l
+// that accepts: a warp ballot and a shared-memory atomicMin find it, and one
+// barrier per accepted flip publishes it with its flip factors.
 #include "hfq_delayed.cuh"
 #include "hfq_device.cuh"
 #include "hfq_gj.cuh"
@@ -21,7 +29,11 @@
 
 namespace hfq {
 
-__global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
+constexpr int kRowsPerThread = 4;  // rows t/2 + 128 q, q < 4: L <= 512
+constexpr int kRowStride = kDelNT / 2;
+constexpr int kNoSlice = 0x7fffffff;
+
+__global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   constexpr int NT = kDelNT;
   constexpr int NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -29,6 +41,8 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
   __shared__ int redi[NW];
   __shared__ double s_inv;
   __shared__ int s_piv, s_item;
+  __shared__ int s_next[3];  // next accepted slice, triple-buffered (see take_next)
+  __shared__ int s_bad;
   __shared__ uint32_t s_tmem_base;
   __shared__ __align__(8) unsigned long long s_mbar;
 
@@ -64,8 +78,7 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
     }
     float* Pu = reinterpret_cast<float*>(smem + lay.off_U);  // [2][L][KP]: spin-major U panels
     float* Pw = reinterpret_cast<float*>(smem + lay.off_W);  // [2][L][KP]: W panels
-    float* diag = reinterpret_cast<float*>(smem + lay.off_diag);
-    float* us = reinterpret_cast<float*>(smem + lay.off_u);  // uniforms rounded to FP32
+    float* fac = reinterpret_cast<float*>(smem + lay.off_diag);  // [L][2]: flip factors of candidates
     double* colk = reinterpret_cast<double*>(smem + lay.off_colk);
     int8_t* ss = reinterpret_cast<int8_t*>(smem + lay.off_s);
     unsigned char* stage = smem + lay.off_stage;
@@ -78,21 +91,47 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
         for (int jj = lane; jj < L; jj += 32) Gu[(size_t)i * ld + jj] = Ggl[(size_t)i * L + jj];
     }
     for (int l = tid; l < L; l += NT) ss[l] = ip.s[l];
+    if (tid < 3) s_next[tid] = kNoSlice;
+    if (tid == 0) s_bad = 0;
     __syncthreads();
-    for (int i = tid; i < L; i += NT) {
-      diag[i] = Gu[(size_t)i * ld + i];
-      diag[L + i] = Gd[(size_t)i * ld + i];
+
+    // per-thread row state: this spin's current diagonal, field, this sweep's uniform
+    const int sp = tid & 1;
+    const int row0 = tid >> 1;
+    float dg[kRowsPerThread], uv[kRowsPerThread];
+    int sv[kRowsPerThread];
+    bool lastbad[kRowsPerThread];
+    float* Gs = sp ? Gd : Gu;
+    float* Us = Pu + (size_t)sp * L * KP;
+    float* Ws = Pw + (size_t)sp * L * KP;
+    auto load_diag = [&]() {
+#pragma unroll
+      for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        const int r = row0 + qq * kRowStride;
+        if (r < L) dg[qq] = Gs[(size_t)r * ld + r];
+      }
+    };
+#pragma unroll
+    for (int qq = 0; qq < kRowsPerThread; ++qq) {
+      const int r = row0 + qq * kRowStride;
+      sv[qq] = r < L ? ss[r] : 1;
+      uv[qq] = 0.f;
+      lastbad[qq] = false;
+      dg[qq] = 0.f;
     }
+    load_diag();
+
     const ChainCounters c0 = *ip.cnt;
     long long n_acc = c0.accepted;
     long long n_rec = 0, n_bad = 0;
     unsigned long long hash = c0.hash;
     double drift = c0.drift;
     const long long n_sweeps = a.n_warm + a.n_meas;
-    int j = 0;  // pending flips in the panels
+    int j = 0;     // pending flips in the panels
+    int par = 0;   // s_next buffer of the current round
     __syncthreads();
 
-    // G += U W^T for both spins, then the diagonal is re-read from G.
+    // G += U W^T for both spins, then the diagonals are re-read from G.
     auto flush = [&]() {
       if (j == 0) return;
       if (use_tc)
@@ -100,92 +139,126 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
       else
         flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
       __syncthreads();
-      for (int i = tid; i < L; i += NT) {
-        diag[i] = Gu[(size_t)i * ld + i];
-        diag[L + i] = Gd[(size_t)i * ld + i];
-      }
+      load_diag();
       j = 0;
       __syncthreads();
     };
 
+    // Evaluates the owned slices r >= lo as proposals with the current
+    // diagonals of both spins (partner threads swap theirs); the lowest
+    // accepting slice of the CTA lands in s_next[par] (read after the next
+    // barrier), its flip factors in fac[2r], fac[2r+1].
+    auto propose = [&](int lo) {
+      int cand = kNoSlice;
+#pragma unroll
+      for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        const int r = row0 + qq * kRowStride;
+        const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
+        const float gu = sp ? other : dg[qq];
+        const float gd = sp ? dg[qq] : other;
+        bool acc = false, bad = false;
+        if (r < L && r >= lo) {
+          acc = del_decide(d0, d1, gu, gd, sv[qq], uv[qq], rule, &bad);
+          if (acc && sp == 0) {
+            float fu, fd;
+            del_factors(d0, d1, gu, gd, sv[qq], &fu, &fd);
+            fac[2 * r] = fu;
+            fac[2 * r + 1] = fd;
+          }
+        }
+        lastbad[qq] = bad && sp == 0;
+        const unsigned b = __ballot_sync(0xffffffffu, acc) & 0x55555555u;
+        if (b && cand == kNoSlice) cand = qq * kRowStride + warp * 16 + ((__ffs(b) - 1) >> 1);
+      }
+      if (lane == 0 && cand != kNoSlice) atomicMin(&s_next[par], cand);
+    };
+
+    // After the barrier of a round: read the decision and reset the buffer
+    // that the round before used (every thread has read it before reaching
+    // this round's barrier, and it is written again only two rounds later).
+    // Also counts the bad ratios among the proposals this round decided,
+    // i.e. the owned slices in [lo, next].
+    auto take_next = [&](int lo) -> int {
+      const int nxt = s_next[par];
+      if (tid == 0) s_next[(par + 2) % 3] = kNoSlice;
+      par = (par + 1) % 3;
+      const int hi = nxt < L ? nxt : L - 1;
+#pragma unroll
+      for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        const int r = row0 + qq * kRowStride;
+        if (r >= lo && r <= hi && lastbad[qq]) ++n_bad;
+      }
+      return nxt;
+    };
+
     for (long long sw = 0; sw < n_sweeps; ++sw) {
       const long long t = c0.t + sw;
-      for (int l = tid; l < L; l += NT)
-        us[l] = (float)proposal_uniform(l, t, ip.chain, ip.grid, a.seed);
+#pragma unroll
+      for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        const int r = row0 + qq * kRowStride;
+        if (r < L) uv[qq] = (float)proposal_uniform(r, t, ip.chain, ip.grid, a.seed);
+      }
+      propose(0);
       __syncthreads();
-      int l0 = 0;
-      while (l0 < L) {
-        // first accepted proposal at or after l0 (every warp evaluates the same window)
-        int first = L;
-        for (int w = l0; w < L; w += 32) {
-          const int l = w + lane;
-          bool acc = false, bad = false;
-          if (l < L) acc = del_decide(d0, d1, diag[l], diag[L + l], ss[l], us[l], rule, &bad);
-          const unsigned b = __ballot_sync(0xffffffffu, acc);
-          const unsigned bb = __ballot_sync(0xffffffffu, bad);
-          if (b) {
-            first = w + __ffs(b) - 1;
-            const int upto = first - w;
-            const unsigned valid = upto >= 31 ? 0xffffffffu : ((2u << upto) - 1u);
-            n_bad += __popc(bb & valid);
-            break;
-          }
-          n_bad += __popc(bb);
-        }
-        if (first >= L) break;
-        const int l = first;
-        const int sl = ss[l];
-        float fu, fd;
-        del_factors(d0, d1, diag[l], diag[L + l], sl, &fu, &fd);
-        // append column j of the panels: item (sp, i) -> u_i, w_i and the diagonal.
-        // Current column / row entries are the base G entry plus a length-j dot
-        // product with the panels (16-byte loads, four partial sums).
-        for (int it = tid; it < 2 * L; it += NT) {
-          const int sp = it >= L;
-          const int i = it - sp * L;
-          const float* G = sp ? Gd : Gu;
-          float* U = Pu + (size_t)sp * L * KP;
-          float* W = Pw + (size_t)sp * L * KP;
-          const float g_il = G[(size_t)i * ld + l];
-          const float g_li = G[(size_t)l * ld + i];
-          const float4* Ui = reinterpret_cast<const float4*>(U + (size_t)i * KP);
-          const float4* Ul = reinterpret_cast<const float4*>(U + (size_t)l * KP);
-          const float4* Wi = reinterpret_cast<const float4*>(W + (size_t)i * KP);
-          const float4* Wl = reinterpret_cast<const float4*>(W + (size_t)l * KP);
+      int l = take_next(0);
+      // flip factors of the accepted slice; read before any flush or
+      // recompute, whose shared-memory workspace may overlay fac[]
+      float fu = 0.f, fd = 0.f;
+      if (l < L) {
+        fu = fac[2 * l];
+        fd = fac[2 * l + 1];
+      }
+      while (l < L) {
+        // append column j of the panels for the owned rows of this thread's spin
+        const float f = sp ? fd : fu;
+#pragma unroll
+        for (int qq = 0; qq < kRowsPerThread; ++qq) {
+          const int i = row0 + qq * kRowStride;
+          if (i >= L) continue;
+          // base G entries first: their latency overlaps the dot products
+          const float gil = Gs[(size_t)i * ld + l], gli = Gs[(size_t)l * ld + i];
           float c4[4] = {0.f, 0.f, 0.f, 0.f}, r4[4] = {0.f, 0.f, 0.f, 0.f};
+          const float4* Ui = reinterpret_cast<const float4*>(Us + (size_t)i * KP);
+          const float4* Wl = reinterpret_cast<const float4*>(Ws + (size_t)l * KP);
+          const float4* Ul = reinterpret_cast<const float4*>(Us + (size_t)l * KP);
+          const float4* Wi = reinterpret_cast<const float4*>(Ws + (size_t)i * KP);
           const int j4 = j >> 2;
-          for (int q = 0; q < j4; ++q) {
-            const float4 ui = Ui[q], wl = Wl[q], ul = Ul[q], wi = Wi[q];
-            c4[0] = __fmaf_rn(ui.x, wl.x, c4[0]);
-            c4[1] = __fmaf_rn(ui.y, wl.y, c4[1]);
-            c4[2] = __fmaf_rn(ui.z, wl.z, c4[2]);
-            c4[3] = __fmaf_rn(ui.w, wl.w, c4[3]);
-            r4[0] = __fmaf_rn(ul.x, wi.x, r4[0]);
-            r4[1] = __fmaf_rn(ul.y, wi.y, r4[1]);
-            r4[2] = __fmaf_rn(ul.z, wi.z, r4[2]);
-            r4[3] = __fmaf_rn(ul.w, wi.w, r4[3]);
+          for (int m4 = 0; m4 < j4; ++m4) {
+            const float4 a1 = Ui[m4], b1 = Wl[m4], a2 = Ul[m4], b2 = Wi[m4];
+            c4[0] = __fmaf_rn(a1.x, b1.x, c4[0]);
+            c4[1] = __fmaf_rn(a1.y, b1.y, c4[1]);
+            c4[2] = __fmaf_rn(a1.z, b1.z, c4[2]);
+            c4[3] = __fmaf_rn(a1.w, b1.w, c4[3]);
+            r4[0] = __fmaf_rn(a2.x, b2.x, r4[0]);
+            r4[1] = __fmaf_rn(a2.y, b2.y, r4[1]);
+            r4[2] = __fmaf_rn(a2.z, b2.z, r4[2]);
+            r4[3] = __fmaf_rn(a2.w, b2.w, r4[3]);
           }
-          const float* Uis = U + (size_t)i * KP;
-          const float* Uls = U + (size_t)l * KP;
-          const float* Wis = W + (size_t)i * KP;
-          const float* Wls = W + (size_t)l * KP;
           for (int m = 4 * j4; m < j; ++m) {
-            c4[0] = __fmaf_rn(Uis[m], Wls[m], c4[0]);
-            r4[0] = __fmaf_rn(Uls[m], Wis[m], r4[0]);
+            c4[0] = __fmaf_rn(Us[(size_t)i * KP + m], Ws[(size_t)l * KP + m], c4[0]);
+            r4[0] = __fmaf_rn(Us[(size_t)l * KP + m], Ws[(size_t)i * KP + m], r4[0]);
           }
-          const float cc = g_il + ((c4[0] + c4[1]) + (c4[2] + c4[3]));
-          const float rr = g_li + ((r4[0] + r4[1]) + (r4[2] + r4[3]));
-          const float uu = cc - (i == l ? 1.f : 0.f);
-          const float ww = rr * (sp ? fd : fu);
-          U[(size_t)i * KP + j] = uu;
-          W[(size_t)i * KP + j] = ww;
-          diag[sp * L + i] = __fmaf_rn(uu, ww, diag[sp * L + i]);
+          const float uu = gil + ((c4[0] + c4[1]) + (c4[2] + c4[3])) - ((i == l) ? 1.f : 0.f);
+          const float ww = (gli + ((r4[0] + r4[1]) + (r4[2] + r4[3]))) * f;
+          Us[(size_t)i * KP + j] = uu;
+          Ws[(size_t)i * KP + j] = ww;
+          dg[qq] = __fmaf_rn(uu, ww, dg[qq]);
+          if (i == l) {
+            sv[qq] = -sv[qq];
+            if (sp == 0) ss[i] = (int8_t)sv[qq];
+          }
         }
-        if (tid == 0) ss[l] = (int8_t)(-sl);
         hash = (hash ^ (unsigned long long)(t * (long long)L + l)) * kFnvPrime;
         ++n_acc;
         ++j;
+        propose(l + 1);
         __syncthreads();
+        const int lnext = take_next(l + 1);
+        float fu_next = 0.f, fd_next = 0.f;
+        if (lnext < L) {
+          fu_next = fac[2 * lnext];
+          fd_next = fac[2 * lnext + 1];
+        }
         if (j == K) flush();
         if (gc.n_wrap > 0 && n_acc % gc.n_wrap == 0) {
           flush();
@@ -211,13 +284,12 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
           }
           drift = fmax(drift, d);
           ++n_rec;
-          for (int i = tid; i < L; i += NT) {
-            diag[i] = Gu[(size_t)i * ld + i];
-            diag[L + i] = Gd[(size_t)i * ld + i];
-          }
+          load_diag();
           __syncthreads();
         }
-        l0 = l + 1;
+        l = lnext;
+        fu = fu_next;
+        fd = fd_next;
       }
       if (sw >= a.n_warm) {
         flush();
@@ -234,7 +306,11 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
           ip.bins[(size_t)b * L + k] += 0.5 * (gu + gd);
         }
         float v = 0.f;
-        for (int l = tid; l < L; l += NT) v += (1.f - diag[l]) * (1.f - diag[L + l]);
+#pragma unroll
+        for (int qq = 0; qq < kRowsPerThread; ++qq) {
+          const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
+          if (sp == 0 && row0 + qq * kRowStride < L) v += (1.f - dg[qq]) * (1.f - other);
+        }
         v = block_sum_f(v, reinterpret_cast<float*>(red));
         if (tid == 0) {
           ip.accD[0] += (double)v / (double)L;
@@ -250,6 +326,13 @@ __global__ void __launch_bounds__(kDelNT, 2) k_sweep_delayed(SweepArgs a) {
         for (int jj = lane; jj < L; jj += 32) Ggl[(size_t)i * L + jj] = Gu[(size_t)i * ld + jj];
     }
     for (int l = tid; l < L; l += NT) ip.s[l] = ss[l];
+    // bad ratios were counted per owned row: sum over the CTA
+    {
+      const int nb = __reduce_add_sync(0xffffffffu, (int)n_bad);
+      if (lane == 0 && nb) atomicAdd(&s_bad, nb);
+      __syncthreads();
+      n_bad = s_bad;
+    }
     if (tid == 0) {
       ChainCounters c = c0;
       c.t = c0.t + n_sweeps;
