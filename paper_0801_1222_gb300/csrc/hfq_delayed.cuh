@@ -369,6 +369,16 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
         const int nM = min(kTileN, L - mb);
         const int N16 = (nM + 15) / 16 * 16;
         stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
+        // this thread's 64 G entries of the tile, loaded before the MMA is
+        // issued so that their latency (L2 when G lives in HBM) overlaps it
+        const int m = 32 * quarter + lane;  // G column nb + m
+        float gpre[64];
+        {
+          const float* g0 = G + (size_t)(mb + 64 * half) * ld + nb + m;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            gpre[q] = (m < nN && 64 * half + q < nM) ? g0[(size_t)q * ld] : 0.f;
+        }
         if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16)) {
           // the tensor core did not signal completion within the limit: flag
           // the context (the host returns HFQMC_ETIMEOUT) and use the CUDA
@@ -378,18 +388,18 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
           __syncthreads();
           return;
         }
-        const int m = 32 * quarter + lane;  // G column nb + m
-        for (int cb = 64 * half; cb < 64 * half + 64 && cb < N16; cb += 16) {
-          float v[16];
-          tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb, v);
-          if (m < nN) {
-            float* g = G + (size_t)(mb + cb) * ld + nb + m;
-            float gv[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) gv[q] = (cb + q < nM) ? g[(size_t)q * ld] : 0.f;
+        for (int c = 0; c < 4; ++c) {
+          const int cb = 64 * half + 16 * c;
+          if (cb < N16) {  // warp-uniform
+            float v[16];
+            tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb, v);
+            if (m < nN) {
+              float* g = G + (size_t)(mb + cb) * ld + nb + m;
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (cb + q < nM) g[(size_t)q * ld] = gv[q] + v[q];
+              for (int q = 0; q < 16; ++q)
+                if (cb + q < nM) g[(size_t)q * ld] = gpre[16 * c + q] + v[q];
+            }
           }
         }
         tc_fence_before();

@@ -18,9 +18,10 @@ namespace hfq {
 // In-place Gauss-Jordan on W = [A | B] (L rows, 2L columns, row-major), in
 // shared or global memory.  colk: L doubles of shared scratch (the pivot
 // column of the current step, so the elimination reads it once per row).
-// The elimination keeps the pivot row in registers and issues the loads of
-// kGjChunk columns of a row before any of their stores, so a warp has that
-// many independent accesses in flight even when W lives in L2.
+// The elimination keeps the pivot row in registers and updates two rows per
+// warp iteration, loading 2 x kGjChunk values before any store, so each warp
+// has that many independent loads and DFMAs in flight (the FP64 pipe's
+// latency is long on this part) whether W lives in shared memory or in L2.
 // On return the right half holds A^{-1} B.  Returns -1 on a zero pivot
 // (uniformly in all threads), 0 otherwise.
 constexpr int kGjChunk = 8;
@@ -94,38 +95,33 @@ __device__ int gj_eliminate(double* W, int L, double* red, int* redi, double* s_
         const int j = c0 + lane + 32 * c;
         rk[c] = j < ld ? wk[j] : 0.0;
       }
-      // rows warp, warp+NW, ...: the loads of the next row are issued before
-      // the stores of the current one, so two rows are in flight per warp
-      double v[kGjChunk];
-      int i = warp;
-      if (i < L) {
+      // two rows per warp iteration: 2 x kGjChunk independent DFMAs between
+      // the loads and the stores, enough to cover the FP64 pipe's latency
+      for (int i = warp; i < L; i += 2 * NW) {
+        const int i2 = i + NW;
+        const bool has2 = i2 < L;
+        double v1[kGjChunk], v2[kGjChunk];
 #pragma unroll
         for (int c = 0; c < kGjChunk; ++c) {
           const int j = c0 + lane + 32 * c;
-          v[c] = j < ld ? W[(size_t)i * ld + j] : 0.0;
+          v1[c] = j < ld ? W[(size_t)i * ld + j] : 0.0;
+          v2[c] = (has2 && j < ld) ? W[(size_t)i2 * ld + j] : 0.0;
         }
-      }
-      for (; i < L; i += NW) {
-        const int inext = i + NW;
-        double vn[kGjChunk];
-        if (inext < L) {
+        const double f1 = (i != k) ? colk[i] : 0.0;
+        const double f2 = (has2 && i2 != k) ? colk[i2] : 0.0;
 #pragma unroll
-          for (int c = 0; c < kGjChunk; ++c) {
-            const int j = c0 + lane + 32 * c;
-            vn[c] = j < ld ? W[(size_t)inext * ld + j] : 0.0;
+        for (int c = 0; c < kGjChunk; ++c) {
+          v1[c] = fma(-f1, rk[c], v1[c]);
+          v2[c] = fma(-f2, rk[c], v2[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kGjChunk; ++c) {
+          const int j = c0 + lane + 32 * c;
+          if (j < ld) {
+            if (i != k) W[(size_t)i * ld + j] = v1[c];
+            if (has2 && i2 != k) W[(size_t)i2 * ld + j] = v2[c];
           }
         }
-        const double f = colk[i];
-        if (i != k && f != 0.0) {
-          double* wi = W + (size_t)i * ld;
-#pragma unroll
-          for (int c = 0; c < kGjChunk; ++c) {
-            const int j = c0 + lane + 32 * c;
-            if (j < ld) wi[j] = fma(-f, rk[c], v[c]);
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < kGjChunk; ++c) v[c] = vn[c];
       }
     }
     __syncthreads();

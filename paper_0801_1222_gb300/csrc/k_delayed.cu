@@ -211,12 +211,20 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       while (l < L) {
         // append column j of the panels for the owned rows of this thread's spin
         const float f = sp ? fd : fu;
+        // base G entries of every owned row first (before any panel store), so
+        // their latency -- L2 when G lives in HBM -- overlaps the dot products
+        float gil_q[kRowsPerThread], gli_q[kRowsPerThread];
+#pragma unroll
+        for (int qq = 0; qq < kRowsPerThread; ++qq) {
+          const int i = row0 + qq * kRowStride;
+          gil_q[qq] = i < L ? Gs[(size_t)i * ld + l] : 0.f;
+          gli_q[qq] = i < L ? Gs[(size_t)l * ld + i] : 0.f;
+        }
 #pragma unroll
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
           const int i = row0 + qq * kRowStride;
           if (i >= L) continue;
-          // base G entries first: their latency overlaps the dot products
-          const float gil = Gs[(size_t)i * ld + l], gli = Gs[(size_t)l * ld + i];
+          const float gil = gil_q[qq], gli = gli_q[qq];
           float c4[4] = {0.f, 0.f, 0.f, 0.f}, r4[4] = {0.f, 0.f, 0.f, 0.f};
           const float4* Ui = reinterpret_cast<const float4*>(Us + (size_t)i * KP);
           const float4* Wl = reinterpret_cast<const float4*>(Ws + (size_t)l * KP);
