@@ -197,14 +197,16 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
                : "memory");
 }
 
+// One bounded poll of the mbarrier phase; the thread may be suspended for up
+// to ~0.1 ms inside try_wait (hint), which frees issue slots while it waits.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(mbar), "r"(phase)
+      : "r"(mbar), "r"(phase), "r"(100000u)
       : "memory");
   return ok != 0;
 }
@@ -289,7 +291,11 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
                                             unsigned char* hi, unsigned char* lo) {
   const int chunks = kTileN * (K8 / 4);
   for (int c = threadIdx.x; c < chunks; c += kDelNT) {
-    const int r = c / (K8 / 4), m0 = (c % (K8 / 4)) * 4;
+    // c = ((row group * K8/4) + k chunk) * 8 + row within group: eight lanes
+    // write one 128-byte core matrix, conflict-free
+    const int r8 = c & 7, rest = c >> 3;
+    const int kc = rest % (K8 / 4), grp = rest / (K8 / 4);
+    const int r = grp * 8 + r8, m0 = kc * 4;
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -330,8 +336,10 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
     }
     tc_commit(tc->mbar);
   }
-  const bool ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
-  // every thread must take the same branch afterwards
+  // warp 0 waits for the commit; the other warps wait at the barrier, which
+  // costs no issue slots.  Every thread takes the same branch afterwards.
+  bool ok_here = true;
+  if (threadIdx.x < 32) ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
   const bool ok = !__syncthreads_or(ok_here ? 0 : 1);
   tc->phase ^= 1u;
   tc_fence_after();
@@ -445,6 +453,29 @@ __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, in
     float acc = 0.f;
     for (int w = 0; w < NW; ++w) acc += part[(size_t)(sp * NW + w) * L + k];
     out[e] = acc;
+  }
+  __syncthreads();
+}
+
+// The same sums for G in shared memory (odd row pitch ld): thread k walks the
+// wrapped diagonal k of both spins in registers; for a fixed l the threads
+// of a warp read rows l+k at stride ld, i.e. 32 different banks.
+__device__ inline void measure_diagonals(const float* Gu, const float* Gd, int ld, int L, float* out) {
+  for (int k = threadIdx.x; k < L; k += kDelNT) {
+    float su = 0.f, sd = 0.f;
+    int l = 0;
+    for (; l + k < L; ++l) {
+      const int o = (l + k) * ld + l;
+      su += Gu[o];
+      sd += Gd[o];
+    }
+    for (; l < L; ++l) {
+      const int o = (l + k - L) * ld + l;
+      su -= Gu[o];
+      sd -= Gd[o];
+    }
+    out[k] = su;
+    out[L + k] = sd;
   }
   __syncthreads();
 }

@@ -128,6 +128,15 @@ __device__ __forceinline__ double proposal_uniform(int l, long long t, int chain
   return u53(x.x, x.y);
 }
 
+// 24-bit uniform in [0,1) from word 0 of the same Philox output that gives
+// the 53-bit uniform (the FP32 paths' proposal threshold; no FP64 involved).
+__device__ __forceinline__ float proposal_uniform_f32(int l, long long t, int chain, int grid,
+                                                      unsigned long long seed) {
+  const uint4 x = philox4x32_10(make_uint4((unsigned)l, (unsigned)t, (unsigned)chain,
+                                           (unsigned)grid), seed);
+  return (float)(x.x >> 8) * (1.0f / 16777216.0f);
+}
+
 __device__ __forceinline__ int8_t initial_spin(int l, int chain, int grid,
                                                unsigned long long seed) {
   const uint4 x = philox4x32_10(make_uint4((unsigned)l | (1u << 16), 0u, (unsigned)chain,

@@ -41,8 +41,8 @@ struct TuneEntry {
   int L_max, k, n_wrap;
 };
 const TuneEntry kTuneTable[] = {
-    {64, 8, 1024},    {128, 16, 2048},  {192, 32, 4096},
-    {256, 32, 4096},  {384, 64, 8192},  {1024, 64, 8192},
+    {64, 8, 8192},     {128, 16, 8192},   {192, 16, 16384},
+    {256, 16, 16384},  {512, 16, 16384},  {1024, 16, 16384},
 };
 
 void tune_lookup(int L, int* k, int* n_wrap) {

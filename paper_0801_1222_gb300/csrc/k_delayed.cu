@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
         const int r = row0 + qq * kRowStride;
-        if (r < L) uv[qq] = (float)proposal_uniform(r, t, ip.chain, ip.grid, a.seed);
+        if (r < L) uv[qq] = proposal_uniform_f32(r, t, ip.chain, ip.grid, a.seed);
       }
       propose(0);
       __syncthreads();
@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
 #pragma unroll
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
           const int i = row0 + qq * kRowStride;
-          gil_q[qq] = i < L ? Gs[(size_t)i * ld + l] : 0.f;
-          gli_q[qq] = i < L ? Gs[(size_t)l * ld + i] : 0.f;
+          gil_q[qq] = i < L ? Gs[i * ld + l] : 0.f;  // 2 L^2 < 2^31: 32-bit offsets
+          gli_q[qq] = i < L ? Gs[l * ld + i] : 0.f;
         }
 #pragma unroll
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
@@ -226,10 +226,11 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           if (i >= L) continue;
           const float gil = gil_q[qq], gli = gli_q[qq];
           float c4[4] = {0.f, 0.f, 0.f, 0.f}, r4[4] = {0.f, 0.f, 0.f, 0.f};
-          const float4* Ui = reinterpret_cast<const float4*>(Us + (size_t)i * KP);
-          const float4* Wl = reinterpret_cast<const float4*>(Ws + (size_t)l * KP);
-          const float4* Ul = reinterpret_cast<const float4*>(Us + (size_t)l * KP);
-          const float4* Wi = reinterpret_cast<const float4*>(Ws + (size_t)i * KP);
+          const int oi = i * KP, ol = l * KP;  // 32-bit shared-memory offsets
+          const float4* Ui = reinterpret_cast<const float4*>(Us + oi);
+          const float4* Wl = reinterpret_cast<const float4*>(Ws + ol);
+          const float4* Ul = reinterpret_cast<const float4*>(Us + ol);
+          const float4* Wi = reinterpret_cast<const float4*>(Ws + oi);
           const int j4 = j >> 2;
           for (int m4 = 0; m4 < j4; ++m4) {
             const float4 a1 = Ui[m4], b1 = Wl[m4], a2 = Ul[m4], b2 = Wi[m4];
@@ -243,13 +244,13 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             r4[3] = __fmaf_rn(a2.w, b2.w, r4[3]);
           }
           for (int m = 4 * j4; m < j; ++m) {
-            c4[0] = __fmaf_rn(Us[(size_t)i * KP + m], Ws[(size_t)l * KP + m], c4[0]);
-            r4[0] = __fmaf_rn(Us[(size_t)l * KP + m], Ws[(size_t)i * KP + m], r4[0]);
+            c4[0] = __fmaf_rn(Us[oi + m], Ws[ol + m], c4[0]);
+            r4[0] = __fmaf_rn(Us[ol + m], Ws[oi + m], r4[0]);
           }
           const float uu = gil + ((c4[0] + c4[1]) + (c4[2] + c4[3])) - ((i == l) ? 1.f : 0.f);
           const float ww = (gli + ((r4[0] + r4[1]) + (r4[2] + r4[3]))) * f;
-          Us[(size_t)i * KP + j] = uu;
-          Ws[(size_t)i * KP + j] = ww;
+          Us[oi + j] = uu;
+          Ws[oi + j] = ww;
           dg[qq] = __fmaf_rn(uu, ww, dg[qq]);
           if (i == l) {
             sv[qq] = -sv[qq];
@@ -306,7 +307,10 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         // partial sums in the (idle) staging area, totals in the panels' space
         float* part = reinterpret_cast<float*>(smem + lay.off_stage);
         float* gsum = reinterpret_cast<float*>(smem + lay.off_U);
-        measure_rows(Gu, Gd, ld, L, part, gsum);
+        if (resident)
+          measure_diagonals(Gu, Gd, ld, L, gsum);
+        else
+          measure_rows(Gu, Gd, ld, L, part, gsum);
         for (int k = tid; k < L; k += NT) {
           const double gu = (double)gsum[k] / (double)L, gd = (double)gsum[L + k] / (double)L;
           ip.acc[k] += gu;
