@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
+TRAFFIC_PER_1000_SWEEPS = 5.83e9 + 113.28e9  # dram read + write of one launch (ncu)
 
 
 def parse():
@@ -112,6 +113,22 @@ class Clocks:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def aggregate(local_ms, local_proposals):
+    """Whole-job throughput of independent replicas: the proposals of all ranks
+    divided by the slowest rank's time (max over ranks).  No data-path
+    collective: the chains of different ranks never interact."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_proposals / (local_ms * 1e-3), local_ms
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    p = torch.tensor([float(local_proposals)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return p.item() / (t.item() * 1e-3), t.item()
 
 
 def peaks():
@@ -230,12 +247,7 @@ def run_ours(args, rank, world, local):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * pps * S * args.steps / (total_ms * 1e-3)
+    value, total_ms = aggregate(sum(step_ms), pps * S * args.steps)
     stats = [ctx.get_stats(i) for i in range(len(grids))]
     lib_ms = stats[0]["last_sweep_ms"]
 
@@ -249,10 +261,17 @@ def run_ours(args, rank, world, local):
     pk, pk_kind = peaks()
     tf32_peak = pk["bf16_tflops"] * (1.1 / 2.25)
     achieved = flops_step / (statistics.median(step_ms) * 1e-3) / 1e12
+    # DRAM bytes of one full-size launch (1000 sweeps of this workload), from
+    # the ncu capture summarised in profiles/k_sweep_delayed_multigrid.md
+    traffic = TRAFFIC_PER_1000_SWEEPS if (args.workload == "multigrid_L100_240" and S == 1000
+                                          and args.precision == "f32_delayed" and not args.chains) else None
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": None,
+                "frac": achieved / tf32_peak, "traffic": traffic,
                 "note": f"tf32 peak = {pk_kind} bf16 x 1.1/2.25 (nominal ratio); algorithmic "
-                        "4*Lambda^2 flops per accepted flip"}
+                        "4*Lambda^2 flops per accepted flip; the kernel is latency-bound "
+                        f"(fraction of the FP32 FMA peak {fp32_peak:.1f} TFLOP/s: "
+                        f"{achieved / fp32_peak:.3f})"}
 
     # e2e through the C ABI from pinned host buffers: G0 upload (set_G0, which
     # also rebuilds G in FP64 for every chain), sweeps, G(tau) download

@@ -297,9 +297,13 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
     const int kc = rest % (K8 / 4), grp = rest / (K8 / 4);
     const int r = grp * 8 + r8, m0 = kc * 4;
     uint32_t h[4], l[4];
+    // one 16-byte load per chunk (rows are 16-byte aligned: KP % 4 == 0)
+    float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < nrows && m0 < j) x4 = *reinterpret_cast<const float4*>(P + (row0 + r) * KP + m0);
+    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float x = (r < nrows && m0 + q < j) ? P[(size_t)(row0 + r) * KP + m0 + q] : 0.f;
+      const float x = (m0 + q < j) ? xs[q] : 0.f;
       h[q] = f32_to_tf32_rna(x);
       l[q] = f32_to_tf32_rna(x - __uint_as_float(h[q]));
     }
