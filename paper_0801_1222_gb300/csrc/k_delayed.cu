@@ -107,12 +107,14 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     auto load_diag = [&]() {
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
         const int r = row0 + qq * kRowStride;
         if (r < L) dg[qq] = Gs[(size_t)r * ld + r];
       }
     };
 #pragma unroll
     for (int qq = 0; qq < kRowsPerThread; ++qq) {
+      if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
       const int r = row0 + qq * kRowStride;
       sv[qq] = r < L ? ss[r] : 1;
       uv[qq] = 0.f;
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       int cand = kNoSlice;
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
         const int r = row0 + qq * kRowStride;
         const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
         const float gu = sp ? other : dg[qq];
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       const int hi = nxt < L ? nxt : L - 1;
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
         const int r = row0 + qq * kRowStride;
         if (r >= lo && r <= hi && lastbad[qq]) ++n_bad;
       }
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       const long long t = c0.t + sw;
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
+        if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
         const int r = row0 + qq * kRowStride;
         if (r < L) uv[qq] = proposal_uniform_f32(r, t, ip.chain, ip.grid, a.seed);
       }
@@ -216,12 +221,14 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         float gil_q[kRowsPerThread], gli_q[kRowsPerThread];
 #pragma unroll
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
+          if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
           const int i = row0 + qq * kRowStride;
           gil_q[qq] = i < L ? Gs[i * ld + l] : 0.f;  // 2 L^2 < 2^31: 32-bit offsets
           gli_q[qq] = i < L ? Gs[l * ld + i] : 0.f;
         }
 #pragma unroll
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
+          if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
           const int i = row0 + qq * kRowStride;
           if (i >= L) continue;
           const float gil = gil_q[qq], gli = gli_q[qq];
@@ -320,6 +327,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         float v = 0.f;
 #pragma unroll
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
+          if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
           const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
           if (sp == 0 && row0 + qq * kRowStride < L) v += (1.f - dg[qq]) * (1.f - other);
         }
