@@ -1,0 +1,112 @@
+"""DMFT self-consistency around the multigrid HF-QMC impurity solver (host glue).
+
+The cycle of the paper's Fig. 1(c) for the Bethe lattice with semi-elliptic
+DOS (W = 4, t = 1) at half filling: the impurity problem defined by the bath
+G0 is solved by HF-QMC on every dtau grid at once (the CUDA library), the
+grids' G(tau) are combined into the dtau -> 0 estimate on a fine tau grid
+(multigrid.py), transformed to Matsubara frequencies, and the bath is updated
+by the Bethe self-consistency G0^{-1}(iw) = iw - t^2 G(iw); the new bath is
+sampled on every grid for the next iteration.
+
+Fourier transforms:
+  tau -> iw: G(iw) = int_0^beta e^{iw tau} G(tau) dtau of the cubic spline
+  through the fine-grid values, integrated exactly by parts (boundary terms
+  with the spline's derivatives at 0+ and beta-, then the piecewise-constant
+  third derivative), which builds in the 1/(iw) jump G(0+) + G(beta-) = -1.
+  iw -> tau: G0(tau) = -1/2 + tau(beta - tau)/4
+             + (2/beta) sum_n Re[e^{-iw_n tau}(G0(iw_n) - 1/(iw_n) - 1/(iw_n)^3)],
+  the bath's high-frequency tail being 1/(iw) + t^2/(iw)^3.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.interpolate import CubicSpline
+
+from . import inputs
+from . import multigrid as mg
+
+
+def matsubara(beta: float, n_iw: int) -> np.ndarray:
+    return (2 * np.arange(n_iw) + 1) * np.pi / float(beta)
+
+
+def spline_ft(beta, tau, G, n_iw):
+    """G(iw_n), n = 0..n_iw-1, from G on the uniform grid tau[0] = 0+ .. tau[-1] = beta-."""
+    tau = np.asarray(tau, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    h = tau[1] - tau[0]
+    sp = CubicSpline(tau, G, bc_type="not-a-knot")
+    d1, d2, d3 = sp.derivative(1), sp.derivative(2), sp.derivative(3)
+    s3 = d3(tau[:-1] + 0.5 * h)  # constant third derivative on each interval
+    iw = 1j * matsubara(beta, n_iw)
+    S0, Sb = G[0], G[-1]
+    out = (-(Sb + S0) / iw + (d1(tau[-1]) + d1(tau[0])) / iw ** 2
+           - (d2(tau[-1]) + d2(tau[0])) / iw ** 3)
+    ph = np.exp(np.outer(iw, tau[:-1]))          # n_iw x N
+    out -= (np.exp(iw * h) - 1.0) / iw ** 4 * (ph @ s3)
+    return out
+
+
+def bath_tau(beta, tau, G0_iw):
+    """G0(tau) at the given tau values from its Matsubara values."""
+    tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
+    wn = matsubara(beta, G0_iw.shape[0])
+    iw = 1j * wn
+    rest = G0_iw - 1.0 / iw - 1.0 / iw ** 3
+    out = np.empty(tau.shape[0])
+    for a in range(0, tau.shape[0], 64):
+        t = tau[a:a + 64, None]
+        out[a:a + 64] = (2.0 / beta) * np.real(np.exp(-1j * wn[None, :] * t) * rest[None, :]).sum(axis=1)
+    out += -0.5 + tau * (beta - tau) / 4.0
+    out[tau == 0.0] = -0.5
+    out[tau == beta] = -0.5
+    return out
+
+
+def bethe_update(G_iw, beta):
+    """Bethe self-consistency at half filling, t = 1: G0(iw) = 1 / (iw - G(iw))."""
+    iw = 1j * matsubara(beta, G_iw.shape[0])
+    return 1.0 / (iw - G_iw)
+
+
+def extrapolate_scalar(dtaus, values, errors=None):
+    """Quadratic-in-dtau^2 least-squares extrapolation of a scalar (e.g. D)."""
+    a, sa, _ = mg.extrapolate(dtaus, np.asarray(values)[:, None],
+                              None if errors is None else np.asarray(errors)[:, None])
+    return float(a[0]), float(sa[0])
+
+
+class MultigridDMFT:
+    """Multigrid HF-QMC DMFT on the Bethe lattice.  ``solver`` is an
+    ``hfqmc.HFQMC`` context over the grids ``dtaus`` (one U)."""
+
+    def __init__(self, solver, beta, dtaus, n_fine=1001, n_iw=4096, mix=1.0):
+        self.solver = solver
+        self.beta = float(beta)
+        self.dtaus = list(dtaus)
+        self.Ls = [inputs.grid_size(beta, d) for d in self.dtaus]
+        self.tau_fine = np.linspace(0.0, self.beta, n_fine)
+        self.n_iw = n_iw
+        self.mix = mix
+        self.G0_iw = inputs.bethe_G0_iw(1j * matsubara(self.beta, n_iw))
+        self.history = []
+
+    def bath_on_grid(self, L):
+        return bath_tau(self.beta, np.arange(L) * self.beta / L, self.G0_iw)
+
+    def iterate(self, n_warm, n_meas):
+        for i, L in enumerate(self.Ls):
+            self.solver.set_G0(i, self.bath_on_grid(L))
+        self.solver.sweep(n_warm, n_meas)
+        Gs, Es = zip(*[self.solver.get_G(i) for i in range(len(self.Ls))])
+        Ds = [self.solver.get_D(i) for i in range(len(self.Ls))]
+        ref = lambda t: bath_tau(self.beta, t, self.G0_iw)
+        G_fine, G_err, _ = mg.multigrid_estimate(self.beta, self.dtaus, list(Gs), list(Es),
+                                                 self.tau_fine, ref)
+        G_iw = spline_ft(self.beta, self.tau_fine, G_fine, self.n_iw)
+        new = bethe_update(G_iw, self.beta)
+        self.G0_iw = self.mix * new + (1.0 - self.mix) * self.G0_iw
+        D, D_err = extrapolate_scalar(self.dtaus, [d[0] for d in Ds], [d[1] for d in Ds])
+        rec = dict(G_fine=G_fine, G_err=G_err, G_iw=G_iw, D_grids=[d[0] for d in Ds], D=D, D_err=D_err)
+        self.history.append(rec)
+        return rec

@@ -37,23 +37,30 @@ def bethe_G0_iw(iw: np.ndarray) -> np.ndarray:
     return 1.0 / (iw - G)
 
 
-def bethe_G0_tau(beta: float, L: int, n_matsubara: int = N_MATSUBARA) -> np.ndarray:
-    """G0(tau_k), tau_k = k beta / L, k = 0..L-1 (physical sign, G0(0+) = -1/2)."""
+def bethe_G0_at(beta: float, tau: np.ndarray, n_matsubara: int = N_MATSUBARA) -> np.ndarray:
+    """Non-interacting Bethe bath G0(tau) at arbitrary 0 <= tau <= beta
+    (tau = 0 means 0+, tau = beta means beta-)."""
     beta = float(beta)
+    tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
     n = np.arange(n_matsubara)
     wn = (2 * n + 1) * np.pi / beta
     iw = 1j * wn
     rest = bethe_G0_iw(iw) - 1.0 / iw - 1.0 / iw ** 3
-    tau = np.arange(L) * (beta / L)
-    out = np.empty(L)
+    out = np.empty(tau.shape[0])
     chunk = 64
-    for a in range(0, L, chunk):
+    for a in range(0, tau.shape[0], chunk):
         t = tau[a:a + chunk, None]
         ph = np.exp(-1j * wn[None, :] * t)
         out[a:a + chunk] = (2.0 / beta) * np.real(ph * rest[None, :]).sum(axis=1)
     out += -0.5 + tau * (beta - tau) / 4.0
-    out[0] = -0.5
+    out[tau == 0.0] = -0.5
+    out[tau == beta] = -0.5
     return out
+
+
+def bethe_G0_tau(beta: float, L: int, n_matsubara: int = N_MATSUBARA) -> np.ndarray:
+    """G0(tau_k), tau_k = k beta / L, k = 0..L-1 (physical sign, G0(0+) = -1/2)."""
+    return bethe_G0_at(beta, np.arange(L) * (float(beta) / L), n_matsubara)
 
 
 def atomic_G0_tau(L: int) -> np.ndarray:

@@ -1,0 +1,80 @@
+"""Multigrid dtau -> 0 estimate of the impurity Green function (host glue).
+
+The paper's "Multigrid HF-QMC method" section obtains an unbiased G from the
+HF-QMC results G_dtau_i of several grids in two steps: (i) each discrete
+estimate is interpolated onto a common fine tau grid with the help of a
+reference model; (ii) at every fine tau point a least-squares fit quadratic
+in dtau^2 is extrapolated to dtau = 0.
+
+Reference model: the paper points to another work for it.  Here the
+reference is a continuous-tau function supplied by the caller -- by default
+the bath G0(tau) of the same impurity problem, which carries the steep
+structure near tau = 0 and beta -- and the difference G_dtau - ref, smooth,
+is interpolated by a natural cubic spline through the grid points tau_k,
+k = 0..Lambda (the last point is beta-).  The fit is
+    G(tau; dtau) = a(tau) + b(tau) dtau^2 + c(tau) dtau^4
+weighted by the error bars, and a(tau) with its standard error is the
+estimate (fewer than three grids: the fit drops to a + b dtau^2).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.interpolate import CubicSpline
+
+
+def grid_taus(beta: float, L: int) -> np.ndarray:
+    """tau_k = k beta / L, k = 0..L (k = L is beta-)."""
+    return np.arange(L + 1) * (float(beta) / L)
+
+
+def interpolate_to_fine(beta, G_grid, tau_fine, ref=None):
+    """G_grid: the Lambda+1 values G(tau_k), k = 0..Lambda, of one grid.
+    ref: callable ref(tau) -> array, or None (no reference)."""
+    G_grid = np.asarray(G_grid, dtype=np.float64)
+    L = G_grid.shape[0] - 1
+    tk = grid_taus(beta, L)
+    r_k = ref(tk) if ref is not None else 0.0
+    spline = CubicSpline(tk, G_grid - r_k, bc_type="natural")
+    r_f = ref(tau_fine) if ref is not None else 0.0
+    return spline(tau_fine) + r_f
+
+
+def extrapolate(dtaus, G_fine, err_fine=None):
+    """Weighted least squares in x = dtau^2 at every fine tau point.
+
+    dtaus: n grids; G_fine: n x m values on the fine grid; err_fine: n x m
+    error bars (None: equal weights).  Returns (a, sigma_a, b); sigma_a is
+    propagated from the error bars through the fit, (X^T W X)^{-1}, which
+    stays defined when the fit has no residual degrees of freedom."""
+    x = np.asarray(dtaus, dtype=np.float64) ** 2
+    G_fine = np.asarray(G_fine, dtype=np.float64)
+    n, m = G_fine.shape
+    deg = 2 if n >= 3 else 1
+    a = np.empty(m)
+    sa = np.full(m, np.nan)
+    b = np.empty(m)
+    X = np.vander(x, deg + 1)  # x^deg ... x^0, numpy's polyfit order
+    for t in range(m):
+        w = None
+        if err_fine is not None:
+            e = np.asarray(err_fine)[:, t]
+            w = 1.0 / np.where(e > 0, e, np.min(e[e > 0]) if np.any(e > 0) else 1.0)
+        coef = np.polyfit(x, G_fine[:, t], deg, w=w)
+        a[t] = coef[-1]
+        b[t] = coef[-2]
+        if w is not None:
+            Xw = X * w[:, None]
+            cov = np.linalg.inv(Xw.T @ Xw)
+            sa[t] = np.sqrt(cov[-1, -1])
+    return a, sa, b
+
+
+def multigrid_estimate(beta, dtaus, G_list, err_list, tau_fine, ref=None):
+    """The dtau -> 0 estimate on tau_fine from the per-grid G(tau_k) (each of
+    length Lambda_i + 1) and their error bars (interpolated the same way)."""
+    Gf = np.array([interpolate_to_fine(beta, G, tau_fine, ref) for G in G_list])
+    Ef = None
+    if err_list is not None:
+        Ef = np.array([np.abs(interpolate_to_fine(beta, E, tau_fine, None)) for E in err_list])
+        Ef = np.maximum(Ef, 1e-15)
+    return extrapolate(dtaus, Gf, Ef)
