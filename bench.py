@@ -305,6 +305,19 @@ def run_ours(args, rank, world, local):
         extra["fp64_rank1"] = {"value": pps * S64 / (ms64 * 1e-3), "unit": "proposals/s",
                                "sweeps": S64, "speedup_fp32_delayed": value / (pps * S64 / (ms64 * 1e-3))}
         ctx64.close()
+        # the same FP32 delayed path with the FP64 recompute every 64 accepted
+        # flips (the configurations' own N_wrap), over a short run
+        Sw = max(10, S // 20)
+        ctx_w, _ = make_ctx(hfqmc, inputs, beta, grids, "f32_delayed", argparse.Namespace(
+            k=args.k, n_wrap=64, flush=args.flush), stream, seed=1)
+        ctx_w.sweep(0, 1)
+        ctx_w.sweep(0, Sw)
+        msw = ctx_w.get_stats(0)["last_sweep_ms"]
+        stw = [ctx_w.get_stats(i) for i in range(len(grids))]
+        extra["fp32_delayed_nwrap64"] = {"value": pps * Sw / (msw * 1e-3), "unit": "proposals/s",
+                                         "sweeps": Sw,
+                                         "drift_max": max(st["drift_max"] for st in stw)}
+        ctx_w.close()
         extra["cpu_baseline"] = oracle_sample(grids, beta, args.cpu_seconds)
     line = {"metric": "HS flip proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

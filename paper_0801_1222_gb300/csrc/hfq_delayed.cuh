@@ -26,8 +26,11 @@ struct DelLayout {
   int K8;       // k rounded up to 8 (tf32 MMA K step)
   // head (kept through a recompute): colk, u, s; body: stage, G, panels, diag
   size_t off_colk, off_u, off_s, off_body;
-  size_t off_stage, off_G, off_U, off_W, off_diag, bytes;
+  size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
 };
+
+// G tile buffer of the TMA flush: 128 rows x 128 floats
+constexpr size_t kGTileBytes = (size_t)kTileN * kTileN * 4;
 
 __host__ __device__ inline size_t del_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -37,7 +40,8 @@ __host__ __device__ inline size_t del_stage_bytes(int K) {
   return 4 * (size_t)kTileN * K8 * 4;
 }
 
-__host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem) {
+__host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem,
+                                                bool gtile = false) {
   DelLayout d;
   d.ldS = L | 1;
   d.KP = K + 4;  // 16-byte rows; (K+4) mod 32 spreads 8 rows of a 16-byte load over all banks
@@ -63,6 +67,12 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   o += del_align(2 * (size_t)L * d.KP * 4, 128);
   d.off_diag = o;
   o += del_align(2 * (size_t)L * 4, 128);
+  d.off_gtile = 0;
+  if (gtile) {
+    o = del_align(o, 1024);
+    d.off_gtile = o;
+    o += kGTileBytes;
+  }
   if (gj_smem && d.off_body + gj_smem_bytes(L) > o) o = d.off_body + gj_smem_bytes(L);
   d.bytes = o;
   return d;
@@ -138,8 +148,10 @@ __device__ inline void flush_ffma(float* Gu, float* Gd, int ld, const float* Pu,
 // ---------------------------------------------------------------------------
 struct TcState {
   uint32_t tmem;       // TMEM base address of this CTA's allocation
-  uint32_t mbar;       // shared address of the completion mbarrier
-  uint32_t phase;      // parity of the next completion
+  uint32_t mbar;       // shared address of the MMA completion mbarrier
+  uint32_t phase;      // parity of the next MMA completion
+  uint32_t mbar_g;     // shared address of the G-tile (TMA bulk load) mbarrier
+  uint32_t phase_g;
   int failed;          // a wait gave up: the tensor path is not used again
 };
 
@@ -250,7 +262,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Allocates kTmemCols TMEM columns (warp 0) and initialises the mbarrier.
+// Allocates kTmemCols TMEM columns (warp 0) and initialises the mbarriers
+// (s_mbar[0]: MMA completion, s_mbar[1]: G-tile bulk loads).
 __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long long* s_mbar,
                                 int* status) {
   (void)status;
@@ -263,6 +276,7 @@ __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long lon
   }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -271,6 +285,8 @@ __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long lon
   tc->tmem = *s_tmem;
   tc->mbar = smem_u32(s_mbar);
   tc->phase = 0;
+  tc->mbar_g = smem_u32(s_mbar + 1);
+  tc->phase_g = 0;
   tc->failed = 0;
 }
 
@@ -283,6 +299,27 @@ __device__ inline void tc_teardown(TcState* tc) {
                  "r"(kTmemCols)
                  : "memory");
 }
+
+// TMA bulk copies (cp.async.bulk): global -> shared completing on an mbarrier
+// with a transaction count, and shared -> global in bulk groups.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst_smem),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Writes rows [row0, row0+nrows) of a panel (pitch KP floats, j valid
 // columns) as TF32 hi and lo parts into 128-row core-matrix tiles; rows and
@@ -317,7 +354,7 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
 // Returns false if the completion wait gave up.
 __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, const unsigned char* Alo,
                                        const unsigned char* Bhi, const unsigned char* Blo, int K8,
-                                       int N16) {
+                                       int N16, bool wait_gtile = false) {
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -343,9 +380,13 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
   // warp 0 waits for the commit; the other warps wait at the barrier, which
   // costs no issue slots.  Every thread takes the same branch afterwards.
   bool ok_here = true;
-  if (threadIdx.x < 32) ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
+  if (threadIdx.x < 32) {
+    ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
+    if (wait_gtile) ok_here = mbar_wait_bounded(tc->mbar_g, tc->phase_g) && ok_here;
+  }
   const bool ok = !__syncthreads_or(ok_here ? 0 : 1);
   tc->phase ^= 1u;
+  if (wait_gtile) tc->phase_g ^= 1u;
   tc_fence_after();
   return ok;
 }
@@ -355,13 +396,14 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
 // up to 128 rows of U), so TMEM lane m holds column nb+m of the G tile and
 // the 32 threads of a warp touch 32 consecutive columns of one G row per
 // access (coalesced in HBM, conflict-free in shared memory).
-__device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
-                                     const float* Pw, int KP, int L, int j, unsigned char* stage,
-                                     const DelLayout& lay, int* status) {
-  if (tc->failed) {
-    flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
-    return;
-  }
+// kGT: G lives in HBM and its tiles travel by TMA bulk copies through the
+// shared-memory buffer gtile (rows loaded during the staging and the MMA,
+// stored back in bulk after the epilogue); otherwise every thread loads its
+// 64 entries of the tile before the MMA is issued and stores them after.
+template <bool kGT>
+__device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
+                                            const float* Pw, int KP, int L, int j, unsigned char* stage,
+                                            const DelLayout& lay, int* status, float* gtile) {
   const int K8 = (j + 7) / 8 * 8;
   const size_t tile_bytes = (size_t)kTileN * lay.K8 * 4;
   unsigned char* Ahi = stage;
@@ -380,21 +422,27 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
       for (int mb = 0; mb < L; mb += kTileN) {       // block of G rows = rows of U
         const int nM = min(kTileN, L - mb);
         const int N16 = (nM + 15) / 16 * 16;
-        stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
-        // this thread's 64 G entries of the tile, loaded before the MMA is
-        // issued so that their latency (L2 when G lives in HBM) overlaps it
         const int m = 32 * quarter + lane;  // G column nb + m
-        float gpre[64];
-        {
+        if constexpr (kGT) {
+          if (warp == 0) {
+            if (lane == 0) mbar_expect_tx(tc->mbar_g, (uint32_t)(nM * nN * 4));
+            __syncwarp();
+            for (int r = lane; r < nM; r += 32)
+              bulk_load(smem_u32(gtile + r * kTileN), G + (size_t)(mb + r) * ld + nb, (uint32_t)(nN * 4),
+                        tc->mbar_g);
+          }
+        }
+        stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
+        float gpre[kGT ? 1 : 64];
+        if constexpr (!kGT) {
           const float* g0 = G + (size_t)(mb + 64 * half) * ld + nb + m;
 #pragma unroll
           for (int q = 0; q < 64; ++q)
             gpre[q] = (m < nN && 64 * half + q < nM) ? g0[(size_t)q * ld] : 0.f;
         }
-        if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16)) {
-          // the tensor core did not signal completion within the limit: flag
-          // the context (the host returns HFQMC_ETIMEOUT) and use the CUDA
-          // cores for every later flush of this CTA
+        if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16, kGT)) {
+          // a completion wait gave up: flag the context (the host returns
+          // HFQMC_ETIMEOUT) and use the CUDA cores for every later flush
           if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
           tc->failed = 1;
           __syncthreads();
@@ -407,18 +455,58 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
             float v[16];
             tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb, v);
             if (m < nN) {
-              float* g = G + (size_t)(mb + cb) * ld + nb + m;
+              if constexpr (kGT) {
+                float* gt = gtile + cb * kTileN + m;
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (cb + q < nM) g[(size_t)q * ld] = gpre[16 * c + q] + v[q];
+                for (int q = 0; q < 16; ++q)
+                  if (cb + q < nM) gt[q * kTileN] += v[q];
+              } else {
+                float* g = G + (size_t)(mb + cb) * ld + nb + m;
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                  if (cb + q < nM) g[(size_t)q * ld] = gpre[16 * c + q] + v[q];
+              }
             }
           }
         }
         tc_fence_before();
+        if constexpr (kGT) {
+          // the updated tile goes back by bulk stores; the buffer is free
+          // again once warp 0 has seen the stores read it
+          fence_async_smem();
+          __syncthreads();
+          if (warp == 0) {
+            for (int r = lane; r < nM; r += 32)
+              bulk_store(G + (size_t)(mb + r) * ld + nb, smem_u32(gtile + r * kTileN), (uint32_t)(nN * 4));
+            bulk_commit();
+            bulk_wait_read0();
+          }
+        }
         __syncthreads();
       }
     }
   }
+  if constexpr (kGT) {
+    // every bulk store complete and visible before G is read again
+    if (warp == 0) {
+      bulk_wait0();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+  }
+}
+
+__device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
+                                     const float* Pw, int KP, int L, int j, unsigned char* stage,
+                                     const DelLayout& lay, int* status, float* gtile = nullptr) {
+  if (tc->failed) {
+    flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
+    return;
+  }
+  if (gtile)
+    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, gtile);
+  else
+    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, nullptr);
 }
 
 // Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l}, walked

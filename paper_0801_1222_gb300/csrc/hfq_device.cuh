@@ -35,6 +35,7 @@ struct GridConst {
   int k;           // delay depth (delayed path)
   int n_wrap;      // recompute interval in accepted flips (<= 0: never)
   int gj_smem;     // 1: the FP64 recompute works on [A | M] in shared memory
+  int gtile;       // 1: the delayed flush moves G tiles by TMA bulk copies
   double lambda;   // cosh(lambda) = exp(dtau U / 2)
   double delta[2]; // Delta for sigma*s = +1: e^{-2 lambda} - 1; sigma*s = -1: e^{2 lambda} - 1
   double dV[2];    // e^{sigma lambda s} - 1 for sigma*s = +1 / -1

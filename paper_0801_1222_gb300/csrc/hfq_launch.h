@@ -25,7 +25,7 @@ int rank1_config(bool f64, size_t smem, int* threads, int* ctas_per_sm);
 int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
 
 // delayed rank-k sweep (FP32)
-size_t delayed_smem(int L, int k, bool resident, bool gj_smem);
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile = false);
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm);
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
 

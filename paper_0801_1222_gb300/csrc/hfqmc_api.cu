@@ -30,7 +30,7 @@ thread_local std::string g_create_error;
 
 struct GridHost {
   double U, dtau, lambda;
-  int L, chains, item0, k, n_wrap, resident, gj_smem;
+  int L, chains, item0, k, n_wrap, resident, gj_smem, gtile = 0;
   bool g0_set = false, ever_set = false;
   long long out_off;
 };
@@ -278,7 +278,17 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
       }
       sm = delayed_smem(h.L, h.k, true, h.gj_smem);
       h.resident = sm <= kResidentBudget;
-      if (!h.resident) sm = delayed_smem(h.L, h.k, false, h.gj_smem);
+      h.gtile = 0;
+      if (!h.resident) {
+        sm = delayed_smem(h.L, h.k, false, h.gj_smem);
+        // G tiles of the flush by TMA bulk copies: rows must be 16-byte aligned
+        // (Lambda % 4 == 0) and the 64 KiB tile buffer must fit
+        const size_t smt = delayed_smem(h.L, h.k, false, h.gj_smem, true);
+        if (o.flush != HFQMC_FLUSH_FFMA && h.L % 4 == 0 && smt <= kSmemMax && o.gtile > 0) {
+          h.gtile = 1;
+          sm = smt;
+        }
+      }
     } else {
       sm = rank1_smem(h.L, true, f64, h.gj_smem);
       h.resident = sm <= kResidentBudget;
@@ -295,6 +305,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     q.k = h.k;
     q.n_wrap = h.n_wrap;
     q.gj_smem = h.gj_smem;
+    q.gtile = h.gtile;
     q.lambda = h.lambda;
     q.delta[0] = std::exp(-2.0 * h.lambda) - 1.0;
     q.delta[1] = std::exp(2.0 * h.lambda) - 1.0;

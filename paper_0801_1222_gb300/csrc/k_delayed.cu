@@ -44,12 +44,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   __shared__ int s_next[3];  // next accepted slice, triple-buffered (see take_next)
   __shared__ int s_bad;
   __shared__ uint32_t s_tmem_base;
-  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ __align__(8) unsigned long long s_mbar[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool use_tc = a.flush != 2;
   TcState tc;
-  if (use_tc) tc_setup(&tc, &s_tmem_base, &s_mbar, a.status);
+  if (use_tc) tc_setup(&tc, &s_tmem_base, s_mbar, a.status);
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(a.queue_head, 1);
@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     const GridConst gc = a.grids[ip.grid];
     const int L = gc.L, K = gc.k;
     const bool resident = gc.resident != 0;
-    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0);
+    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0);
+    float* gtile = gc.gtile ? reinterpret_cast<float*>(smem + lay.off_gtile) : nullptr;
 
     float* Ggl = reinterpret_cast<float*>(ip.G);
     float* Gu;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     auto flush = [&]() {
       if (j == 0) return;
       if (use_tc)
-        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status);
+        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status, gtile);
       else
         flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
       __syncthreads();
@@ -369,8 +370,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   if (use_tc) tc_teardown(&tc);
 }
 
-size_t delayed_smem(int L, int k, bool resident, bool gj_smem) {
-  return del_layout(L, k, resident, gj_smem).bytes;
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile) {
+  return del_layout(L, k, resident, gj_smem, gtile).bytes;
 }
 
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {

@@ -45,7 +45,7 @@ class hfqmc_opts(ctypes.Structure):
                 ("drift_fail", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("autotune", ctypes.c_int), ("flush", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("resident_kb", ctypes.c_int), ("gj_smem", ctypes.c_int)]
+                ("resident_kb", ctypes.c_int), ("gj_smem", ctypes.c_int), ("gtile", ctypes.c_int)]
 
 
 class hfqmc_stats(ctypes.Structure):
@@ -242,7 +242,8 @@ class HFQMC:
 
     def __init__(self, beta, U, dtau, chains_per_grid, seed=1, precision="f32_delayed", k=0,
                  n_wrap=0, accept_rule="metropolis", drift_fail=1e-3, flush="auto",
-                 use_graph=True, stream=None, torch_alloc=True, resident_kb=0, gj_smem=0):
+                 use_graph=True, stream=None, torch_alloc=True, resident_kb=0, gj_smem=0,
+                 gtile=0):
         o = hfqmc_default_opts()
         o.precision = PRECISION[precision]
         o.k = int(k)
@@ -253,6 +254,7 @@ class HFQMC:
         o.use_graph = 1 if use_graph else 0
         o.resident_kb = int(resident_kb)
         o.gj_smem = int(gj_smem)
+        o.gtile = int(gtile)
         self._allocator = None
         try:
             import torch
