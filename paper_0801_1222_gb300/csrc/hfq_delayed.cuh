@@ -25,7 +25,7 @@ struct DelLayout {
   int KP;       // row pitch of the FP32 panels (floats)
   int K8;       // k rounded up to 8 (tf32 MMA K step)
   // head (kept through a recompute): colk, u, s; body: stage, G, panels, diag
-  size_t off_colk, off_u, off_s, off_body;
+  size_t off_colk, off_u, off_perm, off_s, off_body;
   size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
 };
 
@@ -50,6 +50,8 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   d.off_colk = o;
   o += del_align((size_t)L * 8, 128);
   d.off_u = o;
+  o += del_align((size_t)L * 4, 128);
+  d.off_perm = o;
   o += del_align((size_t)L * 4, 128);
   d.off_s = o;
   o += del_align((size_t)L, 128);

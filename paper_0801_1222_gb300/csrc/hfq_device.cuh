@@ -40,7 +40,8 @@ struct GridConst {
   double delta[2]; // Delta for sigma*s = +1: e^{-2 lambda} - 1; sigma*s = -1: e^{2 lambda} - 1
   double dV[2];    // e^{sigma lambda s} - 1 for sigma*s = +1 / -1
   float deltaf[2]; // delta[] rounded to FP32 (the FP32 paths' flip factors)
-  const double* M; // bath matrix (FP64, L x L)
+  const double* M;    // bath matrix (FP64, L x L)
+  const double* Minv; // its inverse (FP64, L x L), for the recompute through G^{-1}
 };
 
 struct ChainCounters {
@@ -91,8 +92,8 @@ struct SweepArgs {
   int flush;                 // delayed path: 1 tcgen05, 2 FFMA
 };
 
-// Bytes of shared memory the FP64 recompute needs for [A | M] of size L.
-__host__ __device__ inline size_t gj_smem_bytes(int L) { return 2 * (size_t)L * L * sizeof(double); }
+// Bytes of shared memory the FP64 recompute needs for its L x L workspace.
+__host__ __device__ inline size_t gj_smem_bytes(int L) { return (size_t)L * L * sizeof(double); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two

@@ -314,6 +314,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     q.deltaf[0] = (float)q.delta[0];
     q.deltaf[1] = (float)q.delta[1];
     q.M = nullptr;
+    q.Minv = nullptr;
   }
 
   // device memory: one pool, grid-major per category
@@ -323,11 +324,12 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     off += align256(bytes);
     return o2;
   };
-  std::vector<size_t> offM(n_grids), offG0(n_grids);
+  std::vector<size_t> offM(n_grids), offG0(n_grids), offMinv(n_grids);
   for (int g = 0; g < n_grids; ++g) {
     offM[g] = take(sizeof(double) * (size_t)c->gh[g].L * c->gh[g].L);
     offG0[g] = take(sizeof(double) * (size_t)c->gh[g].L);
   }
+  for (int g = 0; g < n_grids; ++g) offMinv[g] = take(sizeof(double) * (size_t)c->gh[g].L * c->gh[g].L);
   struct ItemOff {
     size_t s, G, ws, acc, bins, accD, cnt;
   };
@@ -382,7 +384,10 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     return bail(cuda_fail(c, e, "cudaMallocHost"));
   (void)acc_begin;
 
-  for (int g = 0; g < n_grids; ++g) c->gc[g].M = (const double*)(c->d_pool + offM[g]);
+  for (int g = 0; g < n_grids; ++g) {
+    c->gc[g].M = (const double*)(c->d_pool + offM[g]);
+    c->gc[g].Minv = (const double*)(c->d_pool + offMinv[g]);
+  }
   c->items.resize(c->n_items);
   for (int g = 0; g < n_grids; ++g)
     for (int ch = 0; ch < c->gh[g].chains; ++ch) {
@@ -491,6 +496,10 @@ int hfqmc_set_G0(hfqmc_ctx* c, int grid, const double* G0_tau) {
   CK(cudaMemcpyAsync(dG0, G0_tau, sizeof(double) * h.L, cudaMemcpyHostToDevice, c->stream));
   int r = launch_bath_matrix(h.L, dG0, dM, c->stream);
   if (r) return cuda_fail(c, (cudaError_t)r, "bath matrix kernel");
+  // M^{-1} for the recompute through G^{-1}; chain 0's workspace as scratch
+  r = launch_bath_inverse(h.L, dM, const_cast<double*>(c->gc[grid].Minv), c->items[h.item0].ws,
+                          c->d_status, c->stream);
+  if (r) return cuda_fail(c, (cudaError_t)r, "bath inverse kernel");
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.grids = c->d_grids;

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     float* Pw = reinterpret_cast<float*>(smem + lay.off_W);  // [2][L][KP]: W panels
     float* fac = reinterpret_cast<float*>(smem + lay.off_diag);  // [L][2]: flip factors of candidates
     double* colk = reinterpret_cast<double*>(smem + lay.off_colk);
+    int* perm = reinterpret_cast<int*>(smem + lay.off_perm);
     int8_t* ss = reinterpret_cast<int8_t*>(smem + lay.off_s);
     unsigned char* stage = smem + lay.off_stage;
     const int KP = lay.KP;
@@ -287,17 +288,17 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
                 for (int jj = lane; jj < L; jj += 32) Ggl[(size_t)i * L + jj] = Gu[(size_t)i * ld + jj];
               __syncthreads();
             }
-            d = recompute_green<float, NT>(gc, ss, Ggl, Ggl + (size_t)L * L, L,
-                                           reinterpret_cast<double*>(smem + lay.off_body), red, redi,
-                                           &s_inv, &s_piv, colk, true, a.status);
+            d = recompute_green_inv<float, NT>(gc, ss, Ggl, Ggl + (size_t)L * L, L,
+                                               reinterpret_cast<double*>(smem + lay.off_body), red,
+                                               redi, &s_inv, &s_piv, colk, perm, true, a.status);
             if (resident) {
               for (int i = warp; i < 2 * L; i += NW)
                 for (int jj = lane; jj < L; jj += 32) Gu[(size_t)i * ld + jj] = Ggl[(size_t)i * L + jj];
               __syncthreads();
             }
           } else {
-            d = recompute_green<float, NT>(gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv, colk,
-                                           true, a.status);
+            d = recompute_green_inv<float, NT>(gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv,
+                                               colk, perm, true, a.status);
           }
           drift = fmax(drift, d);
           ++n_rec;

@@ -40,11 +40,13 @@ __host__ __device__ inline int r1_ld_smem(int L) { return L | 1; }
 __host__ __device__ inline size_t r1_align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Dynamic shared-memory layout:
-//   head: colk[L] (double, recompute scratch), u[L] (double), s[L] (int8)
+//   head: colk[L] (double, recompute scratch), u[L] (double), perm[L] (int, pivot order of a
+//   recompute), s[L] (int8)
 //   body: [G^up G^dn (if resident)] diag[2L] col[2L] row[2L]
 // During an FP64 recompute with gj_smem the body is overlaid by [A | M].
 __host__ __device__ inline size_t r1_head_bytes(int L) {
-  return r1_align16((size_t)L * sizeof(double)) * 2 + r1_align16((size_t)L);
+  return r1_align16((size_t)L * sizeof(double)) * 2 + r1_align16((size_t)L * sizeof(int)) +
+         r1_align16((size_t)L);
 }
 __host__ __device__ inline size_t r1_smem_bytes(int L, bool resident, size_t elem, bool gj_smem) {
   size_t b = 0;
@@ -140,6 +142,8 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
     p += r1_align16((size_t)L * sizeof(double));
     double* us = reinterpret_cast<double*>(p);
     p += r1_align16((size_t)L * sizeof(double));
+    int* perm = reinterpret_cast<int*>(p);
+    p += r1_align16((size_t)L * sizeof(int));
     int8_t* ss = reinterpret_cast<int8_t*>(p);
     p += r1_align16((size_t)L);
     unsigned char* body = p;
@@ -250,17 +254,17 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
                 for (int j = lane; j < L; j += 32) Ggl[(size_t)i * L + j] = Gu[(size_t)i * ld + j];
               __syncthreads();
             }
-            d = recompute_green<T, NT>(gc, ss, Ggl, Ggl + (size_t)L * L, L,
-                                       reinterpret_cast<double*>(body), red, redi, &s_inv, &s_piv,
-                                       colk, true, a.status);
+            d = recompute_green_inv<T, NT>(gc, ss, Ggl, Ggl + (size_t)L * L, L,
+                                           reinterpret_cast<double*>(body), red, redi, &s_inv, &s_piv,
+                                           colk, perm, true, a.status);
             if (resident) {
               for (int i = warp; i < 2 * L; i += NW)
                 for (int j = lane; j < L; j += 32) Gu[(size_t)i * ld + j] = Ggl[(size_t)i * L + j];
               __syncthreads();
             }
           } else {
-            d = recompute_green<T, NT>(gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv, colk,
-                                       true, a.status);
+            d = recompute_green_inv<T, NT>(gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv, colk,
+                                           perm, true, a.status);
           }
           drift = fmax(drift, d);
           ++n_rec;

@@ -21,6 +21,44 @@ int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st) 
   return (int)cudaGetLastError();
 }
 
+// colk (L doubles) then perm (L ints), 16-byte aligned, before the workspace
+__host__ __device__ inline size_t init_head_bytes(int L) {
+  return ((size_t)L * sizeof(double) + (size_t)L * sizeof(int) + 15) / 16 * 16;
+}
+
+// M^{-1} of one grid's bath matrix by Gauss-Jordan on [M | 1] (one CTA), W
+// an L x 2L FP64 workspace.
+__global__ void __launch_bounds__(256) k_bath_inverse(int L, const double* __restrict__ M,
+                                                      double* __restrict__ Minv, double* W,
+                                                      int* status) {
+  constexpr int NT = 256, NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double red[NW];
+  __shared__ int redi[NW];
+  __shared__ double s_inv;
+  __shared__ int s_piv;
+  double* colk = reinterpret_cast<double*>(dsm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < L; i += NW)
+    for (int j = lane; j < L; j += 32) {
+      W[(size_t)i * 2 * L + j] = M[(size_t)i * L + j];
+      W[(size_t)i * 2 * L + L + j] = (i == j) ? 1.0 : 0.0;
+    }
+  __syncthreads();
+  if (gj_eliminate<NT>(W, L, red, redi, &s_inv, &s_piv, colk) != 0) {
+    if (threadIdx.x == 0) atomicOr(status, kStatusSingular);
+    return;
+  }
+  for (int i = warp; i < L; i += NW)
+    for (int j = lane; j < L; j += 32) Minv[(size_t)i * L + j] = W[(size_t)i * 2 * L + L + j];
+}
+
+int launch_bath_inverse(int L, const double* M, double* Minv, double* W, int* status,
+                        cudaStream_t st) {
+  k_bath_inverse<<<1, 256, (size_t)L * sizeof(double), st>>>(L, M, Minv, W, status);
+  return (int)cudaGetLastError();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridConst* gptr, int item0,
                                                      int first_time) {
@@ -35,13 +73,14 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
   const GridConst gc = *gptr;
   const int L = gc.L;
   double* colk = reinterpret_cast<double*>(dsm);
-  double* W = gc.gj_smem ? colk + L : ip.ws;
+  int* perm = reinterpret_cast<int*>(colk + L);
+  double* W = gc.gj_smem ? reinterpret_cast<double*>(dsm + init_head_bytes(L)) : ip.ws;
   if (first_time)
     for (int l = tid; l < L; l += NT) ip.s[l] = initial_spin(l, ip.chain, ip.grid, a.seed);
   __syncthreads();
   T* G = reinterpret_cast<T*>(ip.G);
-  recompute_green<T, NT>(gc, ip.s, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk,
-                         false, a.status);
+  recompute_green_inv<T, NT>(gc, ip.s, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk,
+                             perm, false, a.status);
   for (int k = tid; k < 2 * L; k += NT) ip.acc[k] = 0.0;
   for (int k = tid; k < kBins * L; k += NT) ip.bins[k] = 0.0;
   for (int k = tid; k < 1 + kBins; k += NT) ip.accD[k] = 0.0;
@@ -65,7 +104,7 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
 }
 
 size_t init_smem(int L, bool gj_smem) {
-  return (size_t)L * sizeof(double) + (gj_smem ? gj_smem_bytes(L) : 0);
+  return init_head_bytes(L) + (gj_smem ? gj_smem_bytes(L) : 0);
 }
 
 int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item0, int n_chains,
