@@ -89,9 +89,9 @@ typedef struct {
                            0 = default (200), < 0 = never (G stays in HBM/L2) */
     int gj_smem;        /* FP64 recompute on [A | M] in shared memory when it fits (Lambda <= 118):
                            0 = yes, < 0 = never (HBM workspace; lower shared-memory footprint) */
-    int gtile;          /* delayed flush with G in HBM: > 0 = move 128x128 G tiles through shared
-                           memory by TMA bulk copies (one per row) when Lambda % 4 == 0 and the
-                           tile fits; 0 = per-thread loads/stores (default, faster as measured) */
+    int gtile;          /* delayed flush with G in HBM: >= 0 = add each 128x128 product tile to G
+                           by one TMA tensor reduce-add when Lambda % 4 == 0 and the 64 KiB tile
+                           buffer fits (default); < 0 = per-thread loads, adds and stores */
 } hfqmc_opts;
 
 /* Per-grid statistics (hfqmc_get_stats). */

@@ -6,8 +6,11 @@
 //     thread issues tcgen05.mma kind::tf32 (M=128, N<=128, K=8 per
 //     instruction) for hi*hi + hi*lo + lo*hi into a TMEM accumulator,
 //     commits to an mbarrier, and all warps read the tile back with
-//     tcgen05.ld and add it to G.  The dropped lo*lo term and the TF32
-//     rounding of lo leave a relative error ~2^-21 per product.
+//     tcgen05.ld.  With G in HBM the tile goes to a shared-memory buffer and
+//     one TMA tensor reduce-add sends it to G (the addition happens in L2;
+//     the SM never loads G); with G in shared memory the warps add it in
+//     place.  The dropped lo*lo term and the TF32 rounding of lo leave a
+//     relative error ~2^-21 per product.
 //   * flush_ffma -- FP32 FMA on the CUDA cores (4 x 4 register tiles).
 #pragma once
 #include <cstdint>
@@ -29,7 +32,7 @@ struct DelLayout {
   size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
 };
 
-// G tile buffer of the TMA flush: 128 rows x 128 floats
+// product tile buffer of the TMA reduce flush: 128 rows x 128 floats
 constexpr size_t kGTileBytes = (size_t)kTileN * kTileN * 4;
 
 __host__ __device__ inline size_t del_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -152,8 +155,6 @@ struct TcState {
   uint32_t tmem;       // TMEM base address of this CTA's allocation
   uint32_t mbar;       // shared address of the MMA completion mbarrier
   uint32_t phase;      // parity of the next MMA completion
-  uint32_t mbar_g;     // shared address of the G-tile (TMA bulk load) mbarrier
-  uint32_t phase_g;
   int failed;          // a wait gave up: the tensor path is not used again
 };
 
@@ -264,8 +265,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Allocates kTmemCols TMEM columns (warp 0) and initialises the mbarriers
-// (s_mbar[0]: MMA completion, s_mbar[1]: G-tile bulk loads).
+// Allocates kTmemCols TMEM columns (warp 0) and initialises the MMA
+// completion mbarrier s_mbar[0].
 __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long long* s_mbar,
                                 int* status) {
   (void)status;
@@ -278,7 +279,6 @@ __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long lon
   }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -287,8 +287,6 @@ __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long lon
   tc->tmem = *s_tmem;
   tc->mbar = smem_u32(s_mbar);
   tc->phase = 0;
-  tc->mbar_g = smem_u32(s_mbar + 1);
-  tc->phase_g = 0;
   tc->failed = 0;
 }
 
@@ -302,22 +300,17 @@ __device__ inline void tc_teardown(TcState* tc) {
                  : "memory");
 }
 
-// TMA bulk copies (cp.async.bulk): global -> shared completing on an mbarrier
-// with a transaction count, and shared -> global in bulk groups.
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   dst_smem),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
-               : "memory");
+// TMA tensor reduce-add (shared -> global, FP32 add performed in L2) through
+// a 4-D tensor map over the G matrices of all chains of a grid, coordinates
+// {column, row, spin, chain}; completion tracked by bulk async-groups.
+// Boxes that reach past Lambda in a coordinate are clipped by the TMA unit.
+__device__ __forceinline__ void tma_reduce_add_4d(const void* tmap, uint32_t src_smem, int x, int y,
+                                                  int z, int w) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.4d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3, %4}], "
+      "[%5];" ::"l"(tmap),
+      "r"(x), "r"(y), "r"(z), "r"(w), "r"(src_smem)
+      : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
@@ -353,10 +346,13 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
 }
 
 // Issues the 3-pass split-TF32 product of one 128 x N tile over K8 and waits.
-// Returns false if the completion wait gave up.
+// wait_reduce_read: thread 0 also waits (after issuing the MMA) until the
+// TMA reduces in flight have read their shared-memory source, so the product
+// buffer may be rewritten after the return.  Returns false if the completion
+// wait gave up.
 __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, const unsigned char* Alo,
                                        const unsigned char* Bhi, const unsigned char* Blo, int K8,
-                                       int N16, bool wait_gtile = false) {
+                                       int N16, bool wait_reduce_read = false) {
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -378,17 +374,16 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
                   idesc, 1);
     }
     tc_commit(tc->mbar);
+    if (wait_reduce_read) bulk_wait_read0();
   }
   // warp 0 waits for the commit; the other warps wait at the barrier, which
   // costs no issue slots.  Every thread takes the same branch afterwards.
   bool ok_here = true;
   if (threadIdx.x < 32) {
     ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
-    if (wait_gtile) ok_here = mbar_wait_bounded(tc->mbar_g, tc->phase_g) && ok_here;
   }
   const bool ok = !__syncthreads_or(ok_here ? 0 : 1);
   tc->phase ^= 1u;
-  if (wait_gtile) tc->phase_g ^= 1u;
   tc_fence_after();
   return ok;
 }
@@ -398,14 +393,18 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
 // up to 128 rows of U), so TMEM lane m holds column nb+m of the G tile and
 // the 32 threads of a warp touch 32 consecutive columns of one G row per
 // access (coalesced in HBM, conflict-free in shared memory).
-// kGT: G lives in HBM and its tiles travel by TMA bulk copies through the
-// shared-memory buffer gtile (rows loaded during the staging and the MMA,
-// stored back in bulk after the epilogue); otherwise every thread loads its
-// 64 entries of the tile before the MMA is issued and stores them after.
-template <bool kGT>
+// kTR (G in HBM): the warps write the product tile to the shared-memory
+// buffer dtile and thread 0 hands it to one TMA tensor reduce-add (tensor map
+// tmap, coordinates {nb, mb, spin, chain}); G is never loaded by the SM, the
+// reduce of one tile overlaps the staging and MMA of the next, and the flush
+// returns once every reduce is complete and visible.  Otherwise every thread
+// loads its 64 entries of the G tile before the MMA is issued and stores the
+// sums after it.
+template <bool kTR>
 __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                             const float* Pw, int KP, int L, int j, unsigned char* stage,
-                                            const DelLayout& lay, int* status, float* gtile) {
+                                            const DelLayout& lay, int* status, float* dtile,
+                                            const void* tmap, int chain) {
   const int K8 = (j + 7) / 8 * 8;
   const size_t tile_bytes = (size_t)kTileN * lay.K8 * 4;
   unsigned char* Ahi = stage;
@@ -425,27 +424,21 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
         const int nM = min(kTileN, L - mb);
         const int N16 = (nM + 15) / 16 * 16;
         const int m = 32 * quarter + lane;  // G column nb + m
-        if constexpr (kGT) {
-          if (warp == 0) {
-            if (lane == 0) mbar_expect_tx(tc->mbar_g, (uint32_t)(nM * nN * 4));
-            __syncwarp();
-            for (int r = lane; r < nM; r += 32)
-              bulk_load(smem_u32(gtile + r * kTileN), G + (size_t)(mb + r) * ld + nb, (uint32_t)(nN * 4),
-                        tc->mbar_g);
-          }
-        }
         stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
-        float gpre[kGT ? 1 : 64];
-        if constexpr (!kGT) {
+        float gpre[kTR ? 1 : 64];
+        if constexpr (!kTR) {
           const float* g0 = G + (size_t)(mb + 64 * half) * ld + nb + m;
 #pragma unroll
           for (int q = 0; q < 64; ++q)
             gpre[q] = (m < nN && 64 * half + q < nM) ? g0[(size_t)q * ld] : 0.f;
         }
-        if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16, kGT)) {
+        if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16, kTR)) {
           // a completion wait gave up: flag the context (the host returns
           // HFQMC_ETIMEOUT) and use the CUDA cores for every later flush
-          if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+          if (threadIdx.x == 0) {
+            atomicOr(status, kStatusTimeout);
+            if constexpr (kTR) bulk_wait0();
+          }
           tc->failed = 1;
           __syncthreads();
           return;
@@ -456,13 +449,13 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
           if (cb < N16) {  // warp-uniform
             float v[16];
             tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb, v);
-            if (m < nN) {
-              if constexpr (kGT) {
-                float* gt = gtile + cb * kTileN + m;
+            if constexpr (kTR) {
+              // rows >= nM and columns >= nN lie outside G and are clipped
+              float* dt = dtile + cb * kTileN + m;
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                  if (cb + q < nM) gt[q * kTileN] += v[q];
-              } else {
+              for (int q = 0; q < 16; ++q) dt[q * kTileN] = v[q];
+            } else {
+              if (m < nN) {
                 float* g = G + (size_t)(mb + cb) * ld + nb + m;
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
@@ -472,25 +465,22 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
           }
         }
         tc_fence_before();
-        if constexpr (kGT) {
-          // the updated tile goes back by bulk stores; the buffer is free
-          // again once warp 0 has seen the stores read it
-          fence_async_smem();
+        if constexpr (kTR) {
+          fence_async_smem();  // the tile's generic stores, seen by the TMA unit
           __syncthreads();
-          if (warp == 0) {
-            for (int r = lane; r < nM; r += 32)
-              bulk_store(G + (size_t)(mb + r) * ld + nb, smem_u32(gtile + r * kTileN), (uint32_t)(nN * 4));
+          if (threadIdx.x == 0) {
+            tma_reduce_add_4d(tmap, smem_u32(dtile), nb, mb, sp, chain);
             bulk_commit();
-            bulk_wait_read0();
           }
+        } else {
+          __syncthreads();
         }
-        __syncthreads();
       }
     }
   }
-  if constexpr (kGT) {
-    // every bulk store complete and visible before G is read again
-    if (warp == 0) {
+  if constexpr (kTR) {
+    // every reduce complete and visible before G is read again
+    if (threadIdx.x == 0) {
       bulk_wait0();
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
@@ -500,15 +490,16 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
 
 __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                      const float* Pw, int KP, int L, int j, unsigned char* stage,
-                                     const DelLayout& lay, int* status, float* gtile = nullptr) {
+                                     const DelLayout& lay, int* status, float* dtile = nullptr,
+                                     const void* tmap = nullptr, int chain = 0) {
   if (tc->failed) {
     flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
     return;
   }
-  if (gtile)
-    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, gtile);
+  if (dtile)
+    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, dtile, tmap, chain);
   else
-    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, nullptr);
+    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, nullptr, nullptr, 0);
 }
 
 // Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l}, walked

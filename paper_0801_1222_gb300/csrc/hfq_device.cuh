@@ -35,13 +35,15 @@ struct GridConst {
   int k;           // delay depth (delayed path)
   int n_wrap;      // recompute interval in accepted flips (<= 0: never)
   int gj_smem;     // 1: the FP64 recompute works on [A | M] in shared memory
-  int gtile;       // 1: the delayed flush moves G tiles by TMA bulk copies
+  int gtile;       // 1: the delayed flush adds its tiles to G by TMA reduce (tmapG)
   double lambda;   // cosh(lambda) = exp(dtau U / 2)
   double delta[2]; // Delta for sigma*s = +1: e^{-2 lambda} - 1; sigma*s = -1: e^{2 lambda} - 1
   double dV[2];    // e^{sigma lambda s} - 1 for sigma*s = +1 / -1
   float deltaf[2]; // delta[] rounded to FP32 (the FP32 paths' flip factors)
   const double* M;    // bath matrix (FP64, L x L)
   const double* Minv; // its inverse (FP64, L x L), for the recompute through G^{-1}
+  const void* tmapG;  // TMA tensor map (CUtensorMap, global memory) over the FP32 G of
+                      // all chains: dims {column, row, spin, chain}; null unless gtile
 };
 
 struct ChainCounters {

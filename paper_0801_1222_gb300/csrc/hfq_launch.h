@@ -25,7 +25,8 @@ size_t rank1_smem(int L, bool resident, bool f64, bool gj_smem);
 int rank1_config(bool f64, size_t smem, int* threads, int* ctas_per_sm);
 int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
 
-// delayed rank-k sweep (FP32)
+// delayed rank-k sweep (FP32); kDelayedTile: edge of the flush's output tiles
+constexpr int kDelayedTile = 128;
 size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile = false);
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm);
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);

@@ -12,11 +12,13 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>  // CUtensorMap and the cuTensorMapEncodeTiled prototype
 
 #include "../../include/hfqmc.h"
 #include "hfq_device.cuh"
@@ -58,6 +60,24 @@ void tune_lookup(int L, int* k, int* n_wrap) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library does not link the driver API).  Null when unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
 }  // namespace
 
 struct hfqmc_ctx {
@@ -85,6 +105,7 @@ struct hfqmc_ctx {
   double* d_outErr = nullptr;
   long long* d_out_off = nullptr;
   unsigned char* d_pool = nullptr;
+  CUtensorMap* d_tmaps = nullptr;  // per grid (used where gh[g].gtile)
   // pinned host mirrors
   GridOut* h_gout = nullptr;
   int* h_status = nullptr;
@@ -281,10 +302,12 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
       h.gtile = 0;
       if (!h.resident) {
         sm = delayed_smem(h.L, h.k, false, h.gj_smem);
-        // G tiles of the flush by TMA bulk copies: rows must be 16-byte aligned
-        // (Lambda % 4 == 0) and the 64 KiB tile buffer must fit
+        // flush by TMA reduce-add: G rows must be 16-byte aligned (Lambda % 4
+        // == 0), the 64 KiB product tile must fit, the driver must encode
+        // the tensor map
         const size_t smt = delayed_smem(h.L, h.k, false, h.gj_smem, true);
-        if (o.flush != HFQMC_FLUSH_FFMA && h.L % 4 == 0 && smt <= kSmemMax && o.gtile > 0) {
+        if (o.flush != HFQMC_FLUSH_FFMA && h.L % 4 == 0 && smt <= kSmemMax && o.gtile >= 0 &&
+            tensor_map_encoder() != nullptr) {
           h.gtile = 1;
           sm = smt;
         }
@@ -315,6 +338,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     q.deltaf[1] = (float)q.delta[1];
     q.M = nullptr;
     q.Minv = nullptr;
+    q.tmapG = nullptr;
   }
 
   // device memory: one pool, grid-major per category
@@ -375,7 +399,8 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   c->d_outG = (double*)dev_alloc(c, sizeof(double) * out_off);
   c->d_outErr = (double*)dev_alloc(c, sizeof(double) * out_off);
   c->d_out_off = (long long*)dev_alloc(c, sizeof(long long) * n_grids);
-  if (!c->d_pool || !c->d_grids || !c->d_items || !c->d_order || !c->d_queue || !c->d_status ||
+  c->d_tmaps = (CUtensorMap*)dev_alloc(c, sizeof(CUtensorMap) * n_grids);
+  if (!c->d_tmaps || !c->d_pool || !c->d_grids || !c->d_items || !c->d_order || !c->d_queue || !c->d_status ||
       !c->d_account || !c->d_gout || !c->d_outG || !c->d_outErr || !c->d_out_off)
     return bail(fail(c, HFQMC_ENOMEM, "device allocation failed (" +
                                           std::to_string(pool_bytes >> 20) + " MiB pool)"));
@@ -388,6 +413,33 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     c->gc[g].M = (const double*)(c->d_pool + offM[g]);
     c->gc[g].Minv = (const double*)(c->d_pool + offMinv[g]);
   }
+  // tensor maps of the TMA reduce flush: the FP32 G of all chains of a grid,
+  // dims {column, row, spin, chain} (the chains' G blocks are consecutive
+  // takes of the pool, a constant stride apart), box 128 x 128 x 1 x 1
+  std::vector<CUtensorMap> tmaps(n_grids);
+  std::memset(tmaps.data(), 0, sizeof(CUtensorMap) * n_grids);
+  for (int g = 0; g < n_grids; ++g) {
+    GridHost& h = c->gh[g];
+    if (!h.gtile) continue;
+    const cuuint64_t L = (cuuint64_t)h.L;
+    const cuuint64_t dims[4] = {L, L, 2, (cuuint64_t)h.chains};
+    const cuuint64_t strides[3] = {L * 4, L * L * 4, (cuuint64_t)align256(2 * L * L * 4)};
+    const cuuint32_t box[4] = {(cuuint32_t)kDelayedTile, (cuuint32_t)kDelayedTile, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    void* base = c->d_pool + io[h.item0].G;
+    if (h.chains > 1 && io[h.item0 + 1].G - io[h.item0].G != strides[2]) h.gtile = 0;
+    if (h.gtile &&
+        tensor_map_encoder()(&tmaps[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      h.gtile = 0;
+    c->gc[g].gtile = h.gtile;
+    c->gc[g].tmapG = h.gtile ? (const void*)(c->d_tmaps + g) : nullptr;
+  }
+  if ((e = cudaMemcpyAsync(c->d_tmaps, tmaps.data(), sizeof(CUtensorMap) * n_grids, cudaMemcpyHostToDevice,
+                           c->stream)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
   c->items.resize(c->n_items);
   for (int g = 0; g < n_grids; ++g)
     for (int ch = 0; ch < c->gh[g].chains; ++ch) {

@@ -29,6 +29,8 @@
 
 namespace hfq {
 
+static_assert(kTileN == kDelayedTile, "tensor-map box and flush tile must agree");
+
 constexpr int kRowsPerThread = 4;  // rows t/2 + 128 q, q < 4: L <= 512
 constexpr int kRowStride = kDelNT / 2;
 constexpr int kNoSlice = 0x7fffffff;
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     const int L = gc.L, K = gc.k;
     const bool resident = gc.resident != 0;
     const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0);
-    float* gtile = gc.gtile ? reinterpret_cast<float*>(smem + lay.off_gtile) : nullptr;
+    // product tile buffer of the TMA reduce flush (G in HBM, tensor map set)
+    float* dtile = gc.gtile ? reinterpret_cast<float*>(smem + lay.off_gtile) : nullptr;
 
     float* Ggl = reinterpret_cast<float*>(ip.G);
     float* Gu;
@@ -139,7 +142,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     auto flush = [&]() {
       if (j == 0) return;
       if (use_tc)
-        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status, gtile);
+        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status, dtile, gc.tmapG,
+                      ip.chain);
       else
         flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
       __syncthreads();
