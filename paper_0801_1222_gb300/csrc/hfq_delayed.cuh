@@ -397,9 +397,9 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
 // buffer dtile and thread 0 hands it to one TMA tensor reduce-add (tensor map
 // tmap, coordinates {nb, mb, spin, chain}); G is never loaded by the SM, the
 // reduce of one tile overlaps the staging and MMA of the next, and the flush
-// returns once every reduce is complete and visible.  Otherwise every thread
-// loads its 64 entries of the G tile before the MMA is issued and stores the
-// sums after it.
+// returns once every reduce is complete and visible.  Otherwise (G in shared
+// memory, or the fallback for G in HBM) every thread adds its 64 entries of
+// the tile in place.
 template <bool kTR>
 __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                             const float* Pw, int KP, int L, int j, unsigned char* stage,
@@ -425,13 +425,6 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
         const int N16 = (nM + 15) / 16 * 16;
         const int m = 32 * quarter + lane;  // G column nb + m
         stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
-        float gpre[kTR ? 1 : 64];
-        if constexpr (!kTR) {
-          const float* g0 = G + (size_t)(mb + 64 * half) * ld + nb + m;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            gpre[q] = (m < nN && 64 * half + q < nM) ? g0[(size_t)q * ld] : 0.f;
-        }
         if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16, kTR)) {
           // a completion wait gave up: flag the context (the host returns
           // HFQMC_ETIMEOUT) and use the CUDA cores for every later flush
@@ -459,7 +452,7 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
                 float* g = G + (size_t)(mb + cb) * ld + nb + m;
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                  if (cb + q < nM) g[(size_t)q * ld] = gpre[16 * c + q] + v[q];
+                  if (cb + q < nM) g[(size_t)q * ld] += v[q];
               }
             }
           }
@@ -502,6 +495,53 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
     flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, nullptr, nullptr, 0);
 }
 
+// One pass of both spins with RB rows per warp in flight and CPL columns per
+// lane (L <= 32 CPL): the RB x CPL loads of a batch are issued before any of
+// them is used; the partial sums are then updated row after row (entries of
+// one row go to distinct k, entries of different rows may share one), so the
+// order of the additions is that of the plain row walk.
+template <int RB, int CPL>
+__device__ __forceinline__ void measure_rows_batched(const float* __restrict__ Gu,
+                                                     const float* __restrict__ Gd, int ld, int L,
+                                                     float* part) {
+  constexpr int NW = kDelNT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int sp = 0; sp < 2; ++sp) {
+    const float* G = sp ? Gd : Gu;
+    float* pw = part + (size_t)(sp * NW + warp) * L;
+    for (int r0 = warp; r0 < L; r0 += NW * RB) {
+      float v[RB][CPL];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int r = r0 + NW * b;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int l = lane + 32 * c;
+          v[b][c] = (r < L && l < L) ? G[(size_t)r * ld + l] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int r = r0 + NW * b;
+        if (r < L) {  // warp-uniform
+          float acc[CPL];
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int l = lane + 32 * c;
+            acc[c] = l < L ? pw[r >= l ? r - l : r - l + L] : 0.f;
+          }
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int l = lane + 32 * c;
+            if (l < L) pw[r >= l ? r - l : r - l + L] = r >= l ? acc[c] + v[b][c] : acc[c] - v[b][c];
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l}, walked
 // row by row: element (r, l) belongs to k = r - l (sign +) or r - l + L
 // (sign -, antiperiodic wrap).  Each warp takes whole rows, lanes take
@@ -517,19 +557,25 @@ __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < 2 * NW * L; e += kDelNT) part[e] = 0.f;
   __syncthreads();
-  for (int sp = 0; sp < 2; ++sp) {
-    const float* G = sp ? Gd : Gu;
-    float* pw = part + (size_t)(sp * NW + warp) * L;
-    for (int r = warp; r < L; r += NW) {
-      const float* gr = G + (size_t)r * ld;
-      for (int l = lane; l < L; l += 32) {
-        const float v = gr[l];
-        if (r >= l)
-          pw[r - l] += v;
-        else
-          pw[r - l + L] -= v;
+  if (L <= 256) {
+    measure_rows_batched<4, 8>(Gu, Gd, ld, L, part);
+  } else if (L <= 512) {
+    measure_rows_batched<2, 16>(Gu, Gd, ld, L, part);
+  } else {
+    for (int sp = 0; sp < 2; ++sp) {
+      const float* G = sp ? Gd : Gu;
+      float* pw = part + (size_t)(sp * NW + warp) * L;
+      for (int r = warp; r < L; r += NW) {
+        const float* gr = G + (size_t)r * ld;
+        for (int l = lane; l < L; l += 32) {
+          const float v = gr[l];
+          if (r >= l)
+            pw[r - l] += v;
+          else
+            pw[r - l + L] -= v;
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   __syncthreads();
