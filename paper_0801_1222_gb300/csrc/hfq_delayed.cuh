@@ -20,7 +20,8 @@
 namespace hfq {
 
 constexpr int kDelNT = 256;          // threads per CTA (8 warps)
-constexpr int kTmemCols = 128;       // TMEM columns per CTA (<= 4 CTAs per SM)
+constexpr int kUBlk = 2;             // U blocks of 128 rows staged (and multiplied) together
+constexpr int kTmemCols = 128 * kUBlk; // TMEM columns per CTA: one accumulator per staged U block
 constexpr int kTileN = 128;          // output tile: 128 rows x 128 columns
 
 struct DelLayout {
@@ -32,15 +33,21 @@ struct DelLayout {
   size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
 };
 
-// product tile buffer of the TMA reduce flush: 128 rows x 128 floats
+// product buffers of the TMA reduce flush: two halves of a tile, 64 rows x
+// 128 floats each, used in turn
 constexpr size_t kGTileBytes = (size_t)kTileN * kTileN * 4;
 
 __host__ __device__ inline size_t del_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// stage: A hi, A lo (128 x K8 each), B hi, B lo (128 x K8 each), tf32 in core-matrix layout
-__host__ __device__ inline size_t del_stage_bytes(int K) {
+// stage: W hi, W lo (one block of 128 rows), then U hi, U lo for up to kUBlk
+// blocks (as many as L has), tf32 in core-matrix layout, 128 x K8 each
+__host__ __device__ inline int del_ublocks(int L) {
+  const int lb = (L + 127) / 128;
+  return lb < kUBlk ? lb : kUBlk;
+}
+__host__ __device__ inline size_t del_stage_bytes(int K, int L) {
   const int K8 = (K + 7) / 8 * 8;
-  return 4 * (size_t)kTileN * K8 * 4;
+  return (size_t)(2 + 2 * del_ublocks(L)) * kTileN * K8 * 4;
 }
 
 __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem,
@@ -63,7 +70,7 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   d.off_stage = o;
   // the staging area doubles as the measurement's per-warp partial sums
   const size_t part = 2 * (size_t)(kDelNT / 32) * L * 4;
-  o += del_align(del_stage_bytes(K) > part ? del_stage_bytes(K) : part, 1024);
+  o += del_align(del_stage_bytes(K, L) > part ? del_stage_bytes(K, L) : part, 1024);
   d.off_G = o;
   if (resident) o += del_align(2 * (size_t)L * d.ldS * 4, 128);
   d.off_U = o;
@@ -314,6 +321,7 @@ __device__ __forceinline__ void tma_reduce_add_4d(const void* tmap, uint32_t src
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Writes rows [row0, row0+nrows) of a panel (pitch KP floats, j valid
@@ -345,43 +353,34 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
   }
 }
 
-// Issues the 3-pass split-TF32 product of one 128 x N tile over K8 and waits.
-// wait_reduce_read: thread 0 also waits (after issuing the MMA) until the
-// TMA reduces in flight have read their shared-memory source, so the product
-// buffer may be rewritten after the return.  Returns false if the completion
-// wait gave up.
-__device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, const unsigned char* Alo,
-                                       const unsigned char* Bhi, const unsigned char* Blo, int K8,
-                                       int N16, bool wait_reduce_read = false) {
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc_fence_after();
-    const uint32_t sbo = (uint32_t)(K8 / 4) * 128u, lbo = 128u;
-    const uint32_t idesc = make_idesc_tf32(N16);
-    const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
-    const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
-    int acc = 0;
-    for (int kb = 0; kb < K8 / 8; ++kb) {
-      const uint32_t koff = (uint32_t)kb * 256u;
-      tc_mma_tf32(tc->tmem, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo),
-                  idesc, acc);
-      acc = 1;
-      tc_mma_tf32(tc->tmem, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_lo + koff, lbo, sbo),
-                  idesc, 1);
-      tc_mma_tf32(tc->tmem, make_smem_desc(a_lo + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo),
-                  idesc, 1);
-    }
-    tc_commit(tc->mbar);
-    if (wait_reduce_read) bulk_wait_read0();
+// Thread 0: issues the 3-pass split-TF32 product of one 128 x N16 tile over
+// K8 into the TMEM accumulator at column col (the caller has fenced and
+// synchronised the staged operands).
+__device__ __forceinline__ void tc_issue_product(const TcState* tc, uint32_t col, const unsigned char* Ahi,
+                                                 const unsigned char* Alo, const unsigned char* Bhi,
+                                                 const unsigned char* Blo, int K8, int N16) {
+  const uint32_t sbo = (uint32_t)(K8 / 4) * 128u, lbo = 128u;
+  const uint32_t idesc = make_idesc_tf32(N16);
+  const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
+  const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+  const uint32_t d = tc->tmem + col;
+  int acc = 0;
+  for (int kb = 0; kb < K8 / 8; ++kb) {
+    const uint32_t koff = (uint32_t)kb * 256u;
+    tc_mma_tf32(d, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo), idesc, acc);
+    acc = 1;
+    tc_mma_tf32(d, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_lo + koff, lbo, sbo), idesc, 1);
+    tc_mma_tf32(d, make_smem_desc(a_lo + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo), idesc, 1);
   }
-  // warp 0 waits for the commit; the other warps wait at the barrier, which
-  // costs no issue slots.  Every thread takes the same branch afterwards.
+}
+
+// All threads: thread 0 commits the products it issued, warp 0 waits for
+// their completion (the other warps wait at the barrier, which costs no issue
+// slots).  Returns false, in every thread, if the wait gave up.
+__device__ inline bool tc_commit_wait(TcState* tc) {
+  if (threadIdx.x == 0) tc_commit(tc->mbar);
   bool ok_here = true;
-  if (threadIdx.x < 32) {
-    ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
-  }
+  if (threadIdx.x < 32) ok_here = mbar_wait_bounded(tc->mbar, tc->phase);
   const bool ok = !__syncthreads_or(ok_here ? 0 : 1);
   tc->phase ^= 1u;
   tc_fence_after();
@@ -393,11 +392,11 @@ __device__ inline bool tc_tile_product(TcState* tc, const unsigned char* Ahi, co
 // up to 128 rows of U), so TMEM lane m holds column nb+m of the G tile and
 // the 32 threads of a warp touch 32 consecutive columns of one G row per
 // access (coalesced in HBM, conflict-free in shared memory).
-// kTR (G in HBM): the warps write the product tile to the shared-memory
-// buffer dtile and thread 0 hands it to one TMA tensor reduce-add (tensor map
-// tmap, coordinates {nb, mb, spin, chain}); G is never loaded by the SM, the
-// reduce of one tile overlaps the staging and MMA of the next, and the flush
-// returns once every reduce is complete and visible.  Otherwise (G in shared
+// kTR (G in HBM): the warps write the product tile, 64 rows at a time, to
+// one of two shared-memory buffers (dtile) and thread 0 hands each half to a
+// TMA tensor reduce-add (tensor map tmap, coordinates {nb, row, spin, chain});
+// G is never loaded by the SM, a reduce streams while the next half is
+// written, and the flush returns once every reduce is complete and visible.  Otherwise (G in shared
 // memory, or the fallback for G in HBM) every thread adds its 64 entries of
 // the tile in place.
 template <bool kTR>
@@ -407,25 +406,42 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
                                             const void* tmap, int chain) {
   const int K8 = (j + 7) / 8 * 8;
   const size_t tile_bytes = (size_t)kTileN * lay.K8 * 4;
-  unsigned char* Ahi = stage;
-  unsigned char* Alo = stage + tile_bytes;
-  unsigned char* Bhi = stage + 2 * tile_bytes;
-  unsigned char* Blo = stage + 3 * tile_bytes;
+  const int LB = (L + kTileN - 1) / kTileN;  // blocks of 128 rows / columns
+  const int UB = del_ublocks(L);             // U blocks staged together
+  unsigned char* Whi = stage;
+  unsigned char* Wlo = stage + tile_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32*quarter.., columns 64*half..
+  const int m = 32 * quarter + lane;               // G column nb + m of a tile
+  int nhalf = 0;                                   // half tiles handed to the TMA unit
   for (int sp = 0; sp < 2; ++sp) {
     float* G = sp ? Gd : Gu;
     const float* U = Pu + (size_t)sp * L * KP;
     const float* W = Pw + (size_t)sp * L * KP;
-    for (int nb = 0; nb < L; nb += kTileN) {         // block of G columns = rows of W
-      const int nN = min(kTileN, L - nb);
-      stage_split(W, KP, nb, nN, j, K8, Ahi, Alo);
-      for (int mb = 0; mb < L; mb += kTileN) {       // block of G rows = rows of U
-        const int nM = min(kTileN, L - mb);
-        const int N16 = (nM + 15) / 16 * 16;
-        const int m = 32 * quarter + lane;  // G column nb + m
-        stage_split(U, KP, mb, nM, j, K8, Bhi, Blo);
-        if (!tc_tile_product(tc, Ahi, Alo, Bhi, Blo, K8, N16, kTR)) {
+    for (int nbi = 0; nbi < LB; ++nbi) {  // block of G columns = rows of W
+      const int nb = nbi * kTileN, nN = min(kTileN, L - nb);
+      stage_split(W, KP, nb, nN, j, K8, Whi, Wlo);
+      for (int mg = 0; mg < LB; mg += UB) {  // group of U blocks = blocks of G rows
+        const int ub = min(UB, LB - mg);
+        if (!(UB == LB && nbi > 0)) {  // all of U staged once per spin when it fits
+          for (int u = 0; u < ub; ++u) {
+            const int mb = (mg + u) * kTileN;
+            stage_split(U, KP, mb, min(kTileN, L - mb), j, K8, stage + (2 + 2 * u) * tile_bytes,
+                        stage + (3 + 2 * u) * tile_bytes);
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          for (int u = 0; u < ub; ++u) {
+            const int nM = min(kTileN, L - (mg + u) * kTileN);
+            tc_issue_product(tc, (uint32_t)(u * kTileN), Whi, Wlo, stage + (2 + 2 * u) * tile_bytes,
+                             stage + (3 + 2 * u) * tile_bytes, K8, (nM + 15) / 16 * 16);
+          }
+        }
+        if (!tc_commit_wait(tc)) {
           // a completion wait gave up: flag the context (the host returns
           // HFQMC_ETIMEOUT) and use the CUDA cores for every later flush
           if (threadIdx.x == 0) {
@@ -436,37 +452,56 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
           __syncthreads();
           return;
         }
+        for (int u = 0; u < ub; ++u) {
+          const int mb = (mg + u) * kTileN, nM = min(kTileN, L - mb);
+          const int N16 = (nM + 15) / 16 * 16;
+          if constexpr (kTR) {
+            // two 64-row halves, each through its own buffer and TMA reduce;
+            // a buffer is rewritten once the reduce issued two halves before
+            // has read it, so one reduce streams while the next half is written
+            for (int r0 = 0; r0 < N16; r0 += kTileN / 2) {
+              float* dbuf = dtile + (size_t)(nhalf & 1) * (kTileN / 2) * kTileN;
+              ++nhalf;
+              if (threadIdx.x == 0) bulk_wait_read1();
+              __syncthreads();
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int cb = 64 * half + 16 * c;
-          if (cb < N16) {  // warp-uniform
-            float v[16];
-            tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb, v);
-            if constexpr (kTR) {
-              // rows >= nM and columns >= nN lie outside G and are clipped
-              float* dt = dtile + cb * kTileN + m;
+              for (int c = 0; c < 2; ++c) {
+                const int cb = r0 + 32 * half + 16 * c;
+                if (cb < N16) {  // warp-uniform
+                  float v[16];
+                  tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(u * kTileN + cb), v);
+                  // rows >= nM and columns >= nN lie outside G and are clipped
+                  float* dt = dbuf + (cb - r0) * kTileN + m;
 #pragma unroll
-              for (int q = 0; q < 16; ++q) dt[q * kTileN] = v[q];
-            } else {
-              if (m < nN) {
-                float* g = G + (size_t)(mb + cb) * ld + nb + m;
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                  if (cb + q < nM) g[(size_t)q * ld] += v[q];
+                  for (int q = 0; q < 16; ++q) dt[q * kTileN] = v[q];
+                }
+              }
+              tc_fence_before();
+              fence_async_smem();  // the half's generic stores, seen by the TMA unit
+              __syncthreads();
+              if (threadIdx.x == 0) {
+                tma_reduce_add_4d(tmap, smem_u32(dbuf), nb, mb + r0, sp, chain);
+                bulk_commit();
               }
             }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int cb = 64 * half + 16 * c;
+              if (cb < N16) {  // warp-uniform: tcgen05.ld is issued by whole warps
+                float v[16];
+                tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(u * kTileN + cb), v);
+                if (m < nN) {
+                  float* g = G + (size_t)(mb + cb) * ld + nb + m;
+#pragma unroll
+                  for (int q = 0; q < 16; ++q)
+                    if (cb + q < nM) g[(size_t)q * ld] += v[q];
+                }
+              }
+            }
+            tc_fence_before();
+            __syncthreads();
           }
-        }
-        tc_fence_before();
-        if constexpr (kTR) {
-          fence_async_smem();  // the tile's generic stores, seen by the TMA unit
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            tma_reduce_add_4d(tmap, smem_u32(dtile), nb, mb, sp, chain);
-            bulk_commit();
-          }
-        } else {
-          __syncthreads();
         }
       }
     }

@@ -415,7 +415,8 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   }
   // tensor maps of the TMA reduce flush: the FP32 G of all chains of a grid,
   // dims {column, row, spin, chain} (the chains' G blocks are consecutive
-  // takes of the pool, a constant stride apart), box 128 x 128 x 1 x 1
+  // takes of the pool, a constant stride apart), box 128 x 64 x 1 x 1 (half a
+  // flush tile)
   std::vector<CUtensorMap> tmaps(n_grids);
   std::memset(tmaps.data(), 0, sizeof(CUtensorMap) * n_grids);
   for (int g = 0; g < n_grids; ++g) {
@@ -424,7 +425,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     const cuuint64_t L = (cuuint64_t)h.L;
     const cuuint64_t dims[4] = {L, L, 2, (cuuint64_t)h.chains};
     const cuuint64_t strides[3] = {L * 4, L * L * 4, (cuuint64_t)align256(2 * L * L * 4)};
-    const cuuint32_t box[4] = {(cuuint32_t)kDelayedTile, (cuuint32_t)kDelayedTile, 1, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)kDelayedTile, (cuuint32_t)kDelayedTile / 2, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     void* base = c->d_pool + io[h.item0].G;
     if (h.chains > 1 && io[h.item0 + 1].G - io[h.item0].G != strides[2]) h.gtile = 0;
