@@ -37,14 +37,16 @@ struct GridHost {
   long long out_off;
 };
 
-// Per-Lambda defaults of the delay depth and recompute interval (the
-// autotuner's table; see autotune.py, which measures and rewrites it).
+// Per-Lambda defaults of the delay depth and recompute interval, measured
+// on GB300: k by the sweep rate at each Lambda (k is lowered further when the
+// panels or the TMA flush buffers would not fit in shared memory), N_wrap by
+// the G(tau) accuracy criterion of the FP32 path against FP64.
 struct TuneEntry {
   int L_max, k, n_wrap;
 };
 const TuneEntry kTuneTable[] = {
-    {64, 8, 8192},     {128, 16, 8192},   {192, 16, 16384},
-    {256, 16, 16384},  {512, 16, 16384},  {1024, 16, 16384},
+    {64, 8, 8192},    {128, 24, 8192},   {144, 16, 16384},
+    {176, 24, 16384}, {1024, 16, 16384},
 };
 
 void tune_lookup(int L, int* k, int* n_wrap) {
@@ -301,16 +303,19 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
       h.resident = sm <= kResidentBudget;
       h.gtile = 0;
       if (!h.resident) {
-        sm = delayed_smem(h.L, h.k, false, h.gj_smem);
         // flush by TMA reduce-add: G rows must be 16-byte aligned (Lambda % 4
-        // == 0), the 64 KiB product tile must fit, the driver must encode
-        // the tensor map
-        const size_t smt = delayed_smem(h.L, h.k, false, h.gj_smem, true);
-        if (o.flush != HFQMC_FLUSH_FFMA && h.L % 4 == 0 && smt <= kSmemMax && o.gtile >= 0 &&
+        // == 0), the 64 KiB product buffers must fit (k is lowered for them
+        // down to 8), the driver must encode the tensor map
+        if (o.flush != HFQMC_FLUSH_FFMA && h.L % 4 == 0 && o.gtile >= 0 &&
             tensor_map_encoder() != nullptr) {
-          h.gtile = 1;
-          sm = smt;
+          int kt = h.k;
+          while (kt > 8 && delayed_smem(h.L, kt, false, h.gj_smem, true) > kSmemMax) kt -= 8;
+          if (delayed_smem(h.L, kt, false, h.gj_smem, true) <= kSmemMax) {
+            h.k = kt;
+            h.gtile = 1;
+          }
         }
+        sm = delayed_smem(h.L, h.k, false, h.gj_smem, h.gtile != 0);
       }
     } else {
       sm = rank1_smem(h.L, true, f64, h.gj_smem);
