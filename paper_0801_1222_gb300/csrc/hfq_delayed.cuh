@@ -39,6 +39,15 @@ constexpr size_t kGTileBytes = (size_t)kTileN * kTileN * 4;
 
 __host__ __device__ inline size_t del_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Offset (floats) from a panel's spin-up block to its spin-down block: L KP
+// rounded up to 16 (mod 32) floats.  The 8 lanes of a 16-byte access in the
+// append read rows i..i+3 of both spins; with KP/4 odd those rows fill four
+// of the eight 16-byte bank groups and the half-bank shift of the other spin
+// fills the remaining four, so the access is conflict-free.
+__host__ __device__ inline int del_spin_stride(int L, int KP) {
+  return L * KP + ((16 - (L * KP) % 32) + 32) % 32;
+}
+
 // stage: W hi, W lo (one block of 128 rows), then U hi, U lo for up to kUBlk
 // blocks (as many as L has), tf32 in core-matrix layout, 128 x K8 each
 __host__ __device__ inline int del_ublocks(int L) {
@@ -74,9 +83,9 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   d.off_G = o;
   if (resident) o += del_align(2 * (size_t)L * d.ldS * 4, 128);
   d.off_U = o;
-  o += del_align(2 * (size_t)L * d.KP * 4, 128);
+  o += del_align((size_t)(del_spin_stride(L, d.KP) + L * d.KP) * 4, 128);
   d.off_W = o;
-  o += del_align(2 * (size_t)L * d.KP * 4, 128);
+  o += del_align((size_t)(del_spin_stride(L, d.KP) + L * d.KP) * 4, 128);
   d.off_diag = o;
   o += del_align(2 * (size_t)L * 4, 128);
   d.off_gtile = 0;
@@ -120,8 +129,8 @@ __device__ inline void flush_ffma(float* Gu, float* Gd, int ld, const float* Pu,
   const int tiles = T4 * T4;
   for (int sp = 0; sp < 2; ++sp) {
     float* G = sp ? Gd : Gu;
-    const float* U = Pu + (size_t)sp * L * KP;
-    const float* W = Pw + (size_t)sp * L * KP;
+    const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
+    const float* W = Pw + (size_t)sp * del_spin_stride(L, KP);
     for (int t = threadIdx.x; t < tiles; t += kDelNT) {
       const int i0 = (t / T4) * 4, c0 = (t % T4) * 4;
       float acc[4][4];
@@ -416,8 +425,8 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   int nhalf = 0;                                   // half tiles handed to the TMA unit
   for (int sp = 0; sp < 2; ++sp) {
     float* G = sp ? Gd : Gu;
-    const float* U = Pu + (size_t)sp * L * KP;
-    const float* W = Pw + (size_t)sp * L * KP;
+    const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
+    const float* W = Pw + (size_t)sp * del_spin_stride(L, KP);
     for (int nbi = 0; nbi < LB; ++nbi) {  // block of G columns = rows of W
       const int nb = nbi * kTileN, nN = min(kTileN, L - nb);
       stage_split(W, KP, nb, nN, j, K8, Whi, Wlo);

@@ -306,20 +306,22 @@ __device__ int gj_invert_inplace(double* B, int L, double* red, int* redi, doubl
   return 0;
 }
 
-// Recomputes G^up and G^dn through the inverse (see above).  W: L x L FP64
+// Recomputes G^up and G^dn through the inverse (see above); [sp_lo, sp_hi)
+// selects the spins (0: up, 1: down).  W: L x L FP64
 // workspace; colk: L doubles and perm: L ints of shared scratch.  Returns the
 // drift max |G_old - G_new| when with_drift, 0 otherwise, -1 after a zero pivot.
 template <typename T, int NT>
 __device__ double recompute_green_inv(const GridConst& gc, const int8_t* s, T* Gup, T* Gdn, int ldG,
                                       double* W, double* red, int* redi, double* s_inv, int* s_piv,
-                                      double* colk, int* perm, bool with_drift, int* status_word) {
+                                      double* colk, int* perm, bool with_drift, int* status_word,
+                                      int sp_lo = 0, int sp_hi = 2) {
   constexpr int NW = NT / 32;
   const int L = gc.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double dmax = 0.0;
   bool finite = true;
   const bool free_bath = gc.lambda == 0.0;
-  for (int sp = 0; sp < 2; ++sp) {
+  for (int sp = sp_lo; sp < sp_hi; ++sp) {
     T* G = sp ? Gdn : Gup;
     const int sig = sp ? -1 : 1;
     const double* src = gc.M;

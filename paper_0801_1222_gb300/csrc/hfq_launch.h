@@ -9,7 +9,7 @@ namespace hfq {
 
 // bath matrix M of one grid from G0(tau_k), and its FP64 inverse
 int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st);
-int launch_bath_inverse(int L, const double* M, double* Minv, double* W, int* status, cudaStream_t st);
+int launch_bath_inverse(int L, const double* M, double* Minv, int* status, cudaStream_t st);
 // initial (or refreshed) field and Green matrices of the chains of one grid
 int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item0, int n_chains,
                        int L, bool f64, bool first_time, bool gj_smem, cudaStream_t st);

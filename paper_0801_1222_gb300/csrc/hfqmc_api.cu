@@ -554,9 +554,8 @@ int hfqmc_set_G0(hfqmc_ctx* c, int grid, const double* G0_tau) {
   CK(cudaMemcpyAsync(dG0, G0_tau, sizeof(double) * h.L, cudaMemcpyHostToDevice, c->stream));
   int r = launch_bath_matrix(h.L, dG0, dM, c->stream);
   if (r) return cuda_fail(c, (cudaError_t)r, "bath matrix kernel");
-  // M^{-1} for the recompute through G^{-1}; chain 0's workspace as scratch
-  r = launch_bath_inverse(h.L, dM, const_cast<double*>(c->gc[grid].Minv), c->items[h.item0].ws,
-                          c->d_status, c->stream);
+  // M^{-1} (closed form of a skew-circulant matrix) for the recompute through G^{-1}
+  r = launch_bath_inverse(h.L, dM, const_cast<double*>(c->gc[grid].Minv), c->d_status, c->stream);
   if (r) return cuda_fail(c, (cudaError_t)r, "bath inverse kernel");
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       Gu = Ggl;
       Gd = Ggl + (size_t)L * L;
     }
-    float* Pu = reinterpret_cast<float*>(smem + lay.off_U);  // [2][L][KP]: spin-major U panels
+    float* Pu = reinterpret_cast<float*>(smem + lay.off_U);  // [2][L][KP] (spin stride padded): U panels
     float* Pw = reinterpret_cast<float*>(smem + lay.off_W);  // [2][L][KP]: W panels
     float* fac = reinterpret_cast<float*>(smem + lay.off_diag);  // [L][2]: flip factors of candidates
     double* colk = reinterpret_cast<double*>(smem + lay.off_colk);
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     int sv[kRowsPerThread];
     bool lastbad[kRowsPerThread];
     float* Gs = sp ? Gd : Gu;
-    float* Us = Pu + (size_t)sp * L * KP;
-    float* Ws = Pw + (size_t)sp * L * KP;
+    float* Us = Pu + (size_t)sp * del_spin_stride(L, KP);
+    float* Ws = Pw + (size_t)sp * del_spin_stride(L, KP);
     auto load_diag = [&]() {
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {

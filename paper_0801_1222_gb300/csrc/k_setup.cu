@@ -21,44 +21,87 @@ int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st) 
   return (int)cudaGetLastError();
 }
 
-// colk (L doubles) then perm (L ints), 16-byte aligned, before the workspace
+// colk (L doubles), perm (L ints) and the field (L int8), 16-byte aligned,
+// before the workspace
 __host__ __device__ inline size_t init_head_bytes(int L) {
-  return ((size_t)L * sizeof(double) + (size_t)L * sizeof(int) + 15) / 16 * 16;
+  return ((size_t)L * sizeof(double) + (size_t)L * sizeof(int) + (size_t)L + 15) / 16 * 16;
 }
 
-// M^{-1} of one grid's bath matrix by Gauss-Jordan on [M | 1] (one CTA), W
-// an L x 2L FP64 workspace.
+// M^{-1} of one grid's bath matrix.  M is skew-circulant: M_{ll'} = c(l - l')
+// with c(d) = -G0(tau_d) and c(d - L) = -c(d) (the antiperiodic wrap).  The
+// plane waves e^{i theta_n l}, theta_n = (2n+1) pi / L (the fermionic
+// Matsubara phases of the grid), diagonalise it with eigenvalues
+//   mu_n = sum_{d<L} c(d) e^{-i theta_n d},
+// so M^{-1} is skew-circulant too, with
+//   c'(d) = (1/L) sum_{n<L} Re[e^{i theta_n d} / mu_n]     (real: mu_{L-1-n} = conj mu_n).
+// One CTA, O(L^2) FP64 work with a table of e^{i pi m / L}, m < 2L.
 __global__ void __launch_bounds__(256) k_bath_inverse(int L, const double* __restrict__ M,
-                                                      double* __restrict__ Minv, double* W,
-                                                      int* status) {
-  constexpr int NT = 256, NW = NT / 32;
+                                                      double* __restrict__ Minv, int* status) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ double red[NW];
-  __shared__ int redi[NW];
-  __shared__ double s_inv;
-  __shared__ int s_piv;
-  double* colk = reinterpret_cast<double*>(dsm);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < L; i += NW)
-    for (int j = lane; j < L; j += 32) {
-      W[(size_t)i * 2 * L + j] = M[(size_t)i * L + j];
-      W[(size_t)i * 2 * L + L + j] = (i == j) ? 1.0 : 0.0;
-    }
+  double* twc = reinterpret_cast<double*>(dsm);  // cos(pi m / L), m < 2L
+  double* tws = twc + 2 * L;                     // sin(pi m / L)
+  double* cc = tws + 2 * L;                      // c(d), d < L
+  double* ir = cc + L;                           // Re 1/mu_n
+  double* ii = ir + L;                           // Im 1/mu_n
+  double* cp = ii + L;                           // c'(d), d < L
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) s_bad = 0;
+  for (int m = tid; m < 2 * L; m += nt) sincospi((double)m / (double)L, &tws[m], &twc[m]);
+  for (int d = tid; d < L; d += nt) cc[d] = M[(size_t)d * L];  // first column
   __syncthreads();
-  if (gj_eliminate<NT>(W, L, red, redi, &s_inv, &s_piv, colk) != 0) {
-    if (threadIdx.x == 0) atomicOr(status, kStatusSingular);
+  for (int n = tid; n < L; n += nt) {
+    const int step = 2 * n + 1;  // phase index (2n+1) d mod 2L, advanced per d
+    double re = 0.0, im = 0.0;
+    int ph = 0;
+    for (int d = 0; d < L; ++d) {
+      re = fma(cc[d], twc[ph], re);
+      im = fma(-cc[d], tws[ph], im);
+      ph += step;
+      if (ph >= 2 * L) ph -= 2 * L;
+    }
+    const double den = re * re + im * im;
+    if (!(den > 0.0) || !isfinite(den)) atomicOr(&s_bad, 1);
+    ir[n] = re / den;
+    ii[n] = -im / den;
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) atomicOr(status, kStatusSingular);
     return;
   }
-  for (int i = warp; i < L; i += NW)
-    for (int j = lane; j < L; j += 32) Minv[(size_t)i * L + j] = W[(size_t)i * 2 * L + L + j];
+  for (int d = tid; d < L; d += nt) {
+    const int step = (2 * d) % (2 * L);  // phase index (2n+1) d mod 2L, advanced per n
+    double acc = 0.0;
+    int ph = d;
+    for (int n = 0; n < L; ++n) {
+      acc = fma(ir[n], twc[ph], acc);
+      acc = fma(-ii[n], tws[ph], acc);
+      ph += step;
+      if (ph >= 2 * L) ph -= 2 * L;
+    }
+    cp[d] = acc / (double)L;
+  }
+  __syncthreads();
+  for (int e = tid; e < L * L; e += nt) {
+    const int i = e / L, j = e - i * L;
+    Minv[e] = i >= j ? cp[i - j] : -cp[i - j + L];
+  }
 }
 
-int launch_bath_inverse(int L, const double* M, double* Minv, double* W, int* status,
-                        cudaStream_t st) {
-  k_bath_inverse<<<1, 256, (size_t)L * sizeof(double), st>>>(L, M, Minv, W, status);
+int launch_bath_inverse(int L, const double* M, double* Minv, int* status, cudaStream_t st) {
+  const size_t smem = 8 * (size_t)L * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024)
+    e = cudaFuncSetAttribute(k_bath_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  k_bath_inverse<<<1, 256, smem, st>>>(L, M, Minv, status);
   return (int)cudaGetLastError();
 }
 
+// Initial (or, after a new bath, rebuilt) Green matrices of every chain of a
+// grid: block (chain, spin), so the two spins of a chain are inverted by two
+// CTAs at once.  The spin-up block also resets the chain's accumulators.
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridConst* gptr, int item0,
                                                      int first_time) {
@@ -68,19 +111,26 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
   __shared__ int redi[NT / 32];
   __shared__ double s_inv;
   __shared__ int s_piv;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, sp = blockIdx.y;
   const ItemPtrs ip = a.items[item0 + blockIdx.x];
   const GridConst gc = *gptr;
   const int L = gc.L;
   double* colk = reinterpret_cast<double*>(dsm);
   int* perm = reinterpret_cast<int*>(colk + L);
-  double* W = gc.gj_smem ? reinterpret_cast<double*>(dsm + init_head_bytes(L)) : ip.ws;
-  if (first_time)
-    for (int l = tid; l < L; l += NT) ip.s[l] = initial_spin(l, ip.chain, ip.grid, a.seed);
+  int8_t* sf = reinterpret_cast<int8_t*>(perm + L);
+  double* W = gc.gj_smem ? reinterpret_cast<double*>(dsm + init_head_bytes(L)) : ip.ws + (size_t)sp * L * L;
+  // the field: drawn afresh (both blocks draw the same values; the spin-up
+  // block stores it) or the chain's current one
+  for (int l = tid; l < L; l += NT) {
+    const int8_t v = first_time ? initial_spin(l, ip.chain, ip.grid, a.seed) : ip.s[l];
+    sf[l] = v;
+    if (first_time && sp == 0) ip.s[l] = v;
+  }
   __syncthreads();
   T* G = reinterpret_cast<T*>(ip.G);
-  recompute_green_inv<T, NT>(gc, ip.s, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk,
-                             perm, false, a.status);
+  recompute_green_inv<T, NT>(gc, sf, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk, perm,
+                             false, a.status, sp, sp + 1);
+  if (sp != 0) return;
   for (int k = tid; k < 2 * L; k += NT) ip.acc[k] = 0.0;
   for (int k = tid; k < kBins * L; k += NT) ip.bins[k] = 0.0;
   for (int k = tid; k < 1 + kBins; k += NT) ip.accD[k] = 0.0;
@@ -114,11 +164,11 @@ int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item
   if (f64) {
     e = cudaFuncSetAttribute(k_init_chains<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    k_init_chains<double><<<n_chains, 256, sm, st>>>(a, d_grid_ptr, item0, first_time ? 1 : 0);
+    k_init_chains<double><<<dim3(n_chains, 2), 256, sm, st>>>(a, d_grid_ptr, item0, first_time ? 1 : 0);
   } else {
     e = cudaFuncSetAttribute(k_init_chains<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    k_init_chains<float><<<n_chains, 256, sm, st>>>(a, d_grid_ptr, item0, first_time ? 1 : 0);
+    k_init_chains<float><<<dim3(n_chains, 2), 256, sm, st>>>(a, d_grid_ptr, item0, first_time ? 1 : 0);
   }
   return (int)cudaGetLastError();
 }
