@@ -130,6 +130,9 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
 
     const ChainCounters c0 = *ip.cnt;
     long long n_acc = c0.accepted;
+    // accepted flips until the next recompute (the cumulative count reaches a
+    // multiple of n_wrap); counted down so the hot loop needs no 64-bit modulo
+    int until_rec = gc.n_wrap > 0 ? (int)(gc.n_wrap - n_acc % gc.n_wrap) : 0;
     long long n_rec = 0, n_bad = 0;
     unsigned long long hash = c0.hash;
     double drift = c0.drift;
@@ -282,7 +285,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           fd_next = fac[2 * lnext + 1];
         }
         if (j == K) flush();
-        if (gc.n_wrap > 0 && n_acc % gc.n_wrap == 0) {
+        if (gc.n_wrap > 0 && --until_rec == 0) {
+          until_rec = gc.n_wrap;
           flush();
           double d;
           if (gc.gj_smem) {

@@ -179,6 +179,9 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
     }
     const ChainCounters c0 = *ip.cnt;
     long long n_acc = c0.accepted;
+    // accepted flips until the next recompute (the cumulative count reaches a
+    // multiple of n_wrap); counted down so the hot loop needs no 64-bit modulo
+    int until_rec = gc.n_wrap > 0 ? (int)(gc.n_wrap - n_acc % gc.n_wrap) : 0;
     long long n_rec = 0, n_bad = 0;
     unsigned long long hash = c0.hash;
     double drift = c0.drift;
@@ -245,7 +248,8 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
         hash = (hash ^ (unsigned long long)(t * (long long)L + first)) * kFnvPrime;
         ++n_acc;
         __syncthreads();
-        if (gc.n_wrap > 0 && n_acc % gc.n_wrap == 0) {
+        if (gc.n_wrap > 0 && --until_rec == 0) {
+          until_rec = gc.n_wrap;
           double d;
           if (gc.gj_smem) {
             // [A | M] overlays the body of shared memory: G goes home to HBM first
