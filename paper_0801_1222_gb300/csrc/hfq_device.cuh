@@ -3,11 +3,11 @@
 // HBM layout (all per context, allocated once at create):
 //   per grid  : GridConst (Lambda, lambda, the two flip factors Delta and the
 //               two bath factors e^{+-lambda}-1), the FP64 bath matrix M
-//               (Lambda x Lambda row-major), GridAccount (measured-sweep
+//               and its inverse (Lambda x Lambda row-major), GridAccount (measured-sweep
 //               counts, 32 bin counts), GridOut (reduced G(tau), errors, D).
 //   per chain : HS field s (int8[Lambda]), G^up and G^dn back to back
 //               (2 x Lambda x Lambda, row-major, FP64 or FP32), the FP64
-//               Gauss-Jordan workspace [A | M] (Lambda x 2 Lambda), the
+//               Gauss-Jordan workspace (Lambda x 2 Lambda; Lambda x Lambda per spin), the
 //               measurement sums (2 Lambda spin-major, 32 x Lambda bins,
 //               1 + 32 D sums) and ChainCounters.
 // Every chain is one work item; items are processed longest-Lambda-first
@@ -34,7 +34,7 @@ struct GridConst {
   int resident;    // 1: G staged in shared memory for the whole chain
   int k;           // delay depth (delayed path)
   int n_wrap;      // recompute interval in accepted flips (<= 0: never)
-  int gj_smem;     // 1: the FP64 recompute works on [A | M] in shared memory
+  int gj_smem;     // 1: the FP64 recompute works in shared memory
   int gtile;       // 1: the delayed flush adds its tiles to G by TMA reduce (tmapG)
   double lambda;   // cosh(lambda) = exp(dtau U / 2)
   double delta[2]; // Delta for sigma*s = +1: e^{-2 lambda} - 1; sigma*s = -1: e^{2 lambda} - 1

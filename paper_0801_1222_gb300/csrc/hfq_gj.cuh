@@ -8,8 +8,7 @@
 // CTA, with per pivot column three barriers (pivot search, row swap + scale,
 // elimination), bound by the FP64 pipe (about 2 DFMA/clk/SM on GB300):
 //  * recompute_green: on the augmented L x 2L matrix [A | M], 1.5 L^3 DFMA
-//    per spin.  Used once per grid for M^{-1} (on [M | 1]) and by the
-//    entry point that allocates nothing.
+//    per spin.  Used by the entry point that allocates nothing.
 //  * recompute_green_inv: G = B^{-1} with B = M^{-1}(1 + D) - D inverted in
 //    place, L^3 DFMA per spin on an L x L workspace -- shared memory when it
 //    fits (Lambda <= 168), the chain's HBM workspace otherwise (L2-resident

@@ -284,7 +284,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     h.k = (o.precision == HFQMC_F32_DELAYED) ? (o.k ? o.k : k_t) : 1;
     h.n_wrap = o.n_wrap ? o.n_wrap : nw_t;
     size_t sm;
-    // the FP64 recompute works in shared memory when [A | M] fits next to the head
+    // the FP64 recompute works in shared memory when its workspace fits next to the head
     h.gj_smem = o.gj_smem >= 0 && gj_smem_bytes(h.L) + 4 * (size_t)h.L * 8 + 1024 <= kSmemMax;
     if (o.precision == HFQMC_F32_DELAYED) {
       if (h.L > 512) {

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           flush();
           double d;
           if (gc.gj_smem) {
-            // [A | M] overlays the body of shared memory: G goes home to HBM first
+            // the FP64 workspace overlays the body of shared memory: G goes home to HBM first
             if (resident) {
               for (int i = warp; i < 2 * L; i += NW)
                 for (int jj = lane; jj < L; jj += 32) Ggl[(size_t)i * L + jj] = Gu[(size_t)i * ld + jj];

@@ -43,7 +43,7 @@ __host__ __device__ inline size_t r1_align16(size_t x) { return (x + 15) & ~(siz
 //   head: colk[L] (double, recompute scratch), u[L] (double), perm[L] (int, pivot order of a
 //   recompute), s[L] (int8)
 //   body: [G^up G^dn (if resident)] diag[2L] col[2L] row[2L]
-// During an FP64 recompute with gj_smem the body is overlaid by [A | M].
+// During an FP64 recompute with gj_smem the body is overlaid by its workspace.
 __host__ __device__ inline size_t r1_head_bytes(int L) {
   return r1_align16((size_t)L * sizeof(double)) * 2 + r1_align16((size_t)L * sizeof(int)) +
          r1_align16((size_t)L);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
           until_rec = gc.n_wrap;
           double d;
           if (gc.gj_smem) {
-            // [A | M] overlays the body of shared memory: G goes home to HBM first
+            // the FP64 workspace overlays the body of shared memory: G goes home to HBM first
             if (resident) {
               for (int i = warp; i < 2 * L; i += NW)
                 for (int j = lane; j < L; j += 32) Ggl[(size_t)i * L + j] = Gu[(size_t)i * ld + j];
