@@ -54,7 +54,8 @@ def extrapolate(dtaus, G_fine, err_fine=None):
     x = np.asarray(dtaus, dtype=np.float64) ** 2
     G_fine = np.asarray(G_fine, dtype=np.float64)
     n, m = G_fine.shape
-    deg = 2 if n >= 3 else 1
+    # one grid: the fixed-dtau value itself (the conventional procedure)
+    deg = 2 if n >= 3 else (1 if n == 2 else 0)
     X = np.vander(x, deg + 1, increasing=True)  # 1, x, x^2
     a = np.empty(m)
     for t in range(m):

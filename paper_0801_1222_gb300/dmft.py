@@ -110,3 +110,33 @@ class MultigridDMFT:
         rec = dict(G_fine=G_fine, G_err=G_err, G_iw=G_iw, D_grids=[d[0] for d in Ds], D=D, D_err=D_err)
         self.history.append(rec)
         return rec
+
+
+class FixedDtauDMFT(MultigridDMFT):
+    """Conventional HF-QMC DMFT at one fixed dtau (the paper's Fig. 1(a) loop):
+    the impurity G on the grid is splined onto the fine tau grid and used as
+    it is, without a dtau -> 0 extrapolation.  ``solver`` holds that one grid."""
+
+    def __init__(self, solver, beta, dtau, n_fine=1001, n_iw=4096, mix=1.0):
+        super().__init__(solver, beta, [dtau], n_fine=n_fine, n_iw=n_iw, mix=mix)
+
+
+def fixed_dtau_sequence(make_solver, beta, dtaus, n_iter, n_warm, n_meas, n_fine=1001, n_iw=4096,
+                        mix=1.0):
+    """Conventional runs for the dtau -> 0 comparison of the "Benchmark
+    results" section: a converged fixed-dtau DMFT loop per dtau (make_solver(dtau)
+    returns a one-grid solver context), then the double occupancy D(dtau)
+    extrapolated quadratically in dtau^2.  Returns (D per dtau, D error per
+    dtau, D extrapolated, its error, the loops)."""
+    loops, Ds, Es = [], [], []
+    for dt in dtaus:
+        solver = make_solver(dt)
+        loop = FixedDtauDMFT(solver, beta, dt, n_fine=n_fine, n_iw=n_iw, mix=mix)
+        for it in range(n_iter):
+            rec = loop.iterate(n_warm, n_meas)
+        Ds.append(rec["D_grids"][0])
+        Es.append(rec["D_err"])
+        loops.append(loop)
+    D0, E0 = extrapolate_scalar(dtaus, Ds, Es)
+    return Ds, Es, D0, E0, loops
+

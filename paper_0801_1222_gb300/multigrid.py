@@ -49,7 +49,9 @@ def extrapolate(dtaus, G_fine, err_fine=None):
     x = np.asarray(dtaus, dtype=np.float64) ** 2
     G_fine = np.asarray(G_fine, dtype=np.float64)
     n, m = G_fine.shape
-    deg = 2 if n >= 3 else 1
+    # a + b x + c x^2 for three or more grids, a + b x for two; one grid is
+    # the conventional fixed-dtau estimate itself (no extrapolation)
+    deg = 2 if n >= 3 else (1 if n == 2 else 0)
     a = np.empty(m)
     sa = np.full(m, np.nan)
     b = np.empty(m)
@@ -61,7 +63,7 @@ def extrapolate(dtaus, G_fine, err_fine=None):
             w = 1.0 / np.where(e > 0, e, np.min(e[e > 0]) if np.any(e > 0) else 1.0)
         coef = np.polyfit(x, G_fine[:, t], deg, w=w)
         a[t] = coef[-1]
-        b[t] = coef[-2]
+        b[t] = coef[-2] if deg > 0 else 0.0
         if w is not None:
             Xw = X * w[:, None]
             cov = np.linalg.inv(Xw.T @ Xw)

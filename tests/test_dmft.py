@@ -70,3 +70,72 @@ def test_gpu_dmft_loop_U0_is_stationary_and_U4_runs():
         rec = loop.iterate(100 if it == 0 else 20, 400)
     assert np.all(np.isfinite(rec["G_fine"])) and 0.0 < rec["D"] < 0.25
     assert abs(rec["G_fine"][0] + 0.5) < 1e-4
+
+
+def test_one_grid_fit_is_the_grid_value():
+    """The conventional (fixed-dtau) procedure: a single grid's values are the
+    estimate, with their own error bars (product and oracle agree)."""
+    from paper_0801_1222_gb300 import multigrid as mg
+    from oracle import multigrid as om
+    vals = np.array([[0.3, -0.2, 0.11]])
+    errs = np.array([[1e-3, 2e-3, 5e-4]])
+    a, sa, b = mg.extrapolate([0.25], vals, errs)
+    np.testing.assert_allclose(a, vals[0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(sa, errs[0], rtol=1e-12)
+    assert np.all(b == 0.0)
+    np.testing.assert_allclose(om.extrapolate([0.25], vals, errs), vals[0], rtol=0, atol=1e-15)
+    D, E = dmft.extrapolate_scalar([0.4], [0.2], [0.01])
+    assert D == 0.2 and abs(E - 0.01) < 1e-15
+
+
+def _oracle_solver(beta, U, dtau, chains=2, seed=3):
+    from oracle import OracleHFQMC
+    return OracleHFQMC(beta, [(U, dtau)], [chains], seed=seed, n_wrap=16)
+
+
+def test_fixed_dtau_dmft_U0_is_stationary_with_the_oracle_solver():
+    """Conventional loop at U = 0: G = G0 on the grid, the spline of G - G0 is
+    zero, so the updated bath is the semicircle again and D = 1/4."""
+    beta, dtau = 4.0, 0.5
+    loop = dmft.FixedDtauDMFT(_oracle_solver(beta, 0.0, dtau), beta, dtau, n_fine=401, n_iw=1024)
+    g0 = loop.G0_iw.copy()
+    rec = loop.iterate(2, 20)
+    # round-off of the bath's Matsubara sum and the spline transform only
+    assert np.max(np.abs(loop.G0_iw - g0)) < 1e-10
+    assert abs(rec["D"] - 0.25) < 1e-12
+
+
+def test_fixed_dtau_sequence_with_the_oracle_solver():
+    """D(dtau) from converged fixed-dtau loops and its dtau^2 extrapolation:
+    physical range, the extrapolation a weighted fit through the points."""
+    beta, U = 2.0, 2.0
+    dtaus = [0.5, 0.4, 0.25]
+    Ds, Es, D0, E0, loops = dmft.fixed_dtau_sequence(
+        lambda dt: _oracle_solver(beta, U, dt, chains=4), beta, dtaus, n_iter=2, n_warm=50,
+        n_meas=400, n_fine=201, n_iw=512, mix=1.0)
+    assert len(Ds) == 3 and all(0.0 < d < 0.25 for d in Ds)
+    assert all(e > 0 for e in Es) and np.isfinite(D0) and E0 > 0
+    # the quadratic fit through three points reproduces them
+    x = np.array(dtaus) ** 2
+    c = np.polyfit(x, Ds, 2)
+    assert abs(c[-1] - D0) < 1e-12
+    for lp in loops:
+        assert abs(lp.history[-1]["G_fine"][0] + 0.5) < 0.05
+
+
+@pytest.mark.gpu
+def test_gpu_fixed_dtau_sequence_U4():
+    from gpu_common import lib
+    h = lib()
+    beta, U = 4.0, 4.0
+    dtaus = [0.5, 0.4, 0.25]
+
+    def make(dt):
+        return h.HFQMC(beta, U, [dt], [32], seed=2, precision="f32_delayed", drift_fail=1.0)
+
+    Ds, Es, D0, E0, loops = dmft.fixed_dtau_sequence(make, beta, dtaus, n_iter=2, n_warm=100,
+                                                     n_meas=400, n_fine=401, n_iw=1024, mix=0.8)
+    assert all(0.0 < d < 0.25 for d in Ds) and np.isfinite(D0) and 0.0 < D0 < 0.25
+    for lp in loops:
+        assert np.all(np.isfinite(lp.history[-1]["G_fine"]))
+        lp.solver.close()
