@@ -95,6 +95,30 @@ def test_G_tau_fp32_within_1e5_of_fp64():
     assert np.all(np.abs(G32 - G64) <= 1e-5 + 3 * sig), np.max(np.abs(G32 - G64) / sig)
 
 
+def test_G_tau_tma_path_within_1e5_of_fp64():
+    """The same bound on the path that keeps G in HBM (Lambda = 160 at the
+    tuned k and N_wrap: TMA reduce flush, batched measurement walk)."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    beta, U, L, nc = 32.0, 5.0, 160, 64
+    g0 = inputs.bethe_G0_tau(beta, L)
+    res = {}
+    for prec in ("f64_rank1", "f32_delayed"):
+        ctx = h.HFQMC(beta, U, [beta / L], [nc], seed=12, precision=prec, drift_fail=1.0,
+                      n_wrap=(1 << 30) if prec == "f64_rank1" else 0)
+        ctx.set_G0(0, g0)
+        ctx.sweep(20, 150)
+        res[prec] = ctx.get_G(0)
+        if prec == "f32_delayed":
+            st = ctx.get_stats(0)
+            assert st["k"] == 24  # G (206 KB) above the 200 KB on-chip budget: in HBM
+        ctx.close()
+    G64, E64 = res["f64_rank1"]
+    G32, E32 = res["f32_delayed"]
+    sig = np.sqrt(E64 ** 2 + E32 ** 2)
+    assert np.all(np.abs(G32 - G64) <= 1e-5 + 3 * sig), np.max(np.abs(G32 - G64) / sig)
+
+
 def test_drift_is_reported_and_bounded():
     from paper_0801_1222_gb300 import inputs
     h = lib()
