@@ -79,7 +79,9 @@ typedef struct {
     double drift_warn;  /* recorded only */
     double drift_fail;  /* hfqmc_sweep returns HFQMC_EDRIFT above this (<= 0: never) */
     void *cuda_stream;  /* cudaStream_t to order all work on; NULL = library-owned stream */
-    int autotune;       /* 1: use the autotuned per-Lambda table for k / n_wrap when 0 */
+    int autotune;       /* 1: k / n_wrap left 0 come from the per-Lambda table (the caller's
+                           tune_table if given, else the built-in one measured on GB300);
+                           0: they default to k = 16 and n_wrap = 1024 */
     int flush;          /* HFQMC_FLUSH_* (F32_DELAYED only) */
     int use_graph;      /* 1: replay hfqmc_sweep's launches as a captured CUDA graph */
     hfqmc_alloc_fn alloc; /* optional device allocator hook (e.g. PyTorch's caching allocator) */
@@ -91,7 +93,13 @@ typedef struct {
                            0 = yes, < 0 = never (HBM workspace; lower shared-memory footprint) */
     int gtile;          /* delayed flush with G in HBM: >= 0 = add each 128x128 product tile to G
                            by one TMA tensor reduce-add when Lambda % 4 == 0 and the 64 KiB tile
-                           buffer fits (default); < 0 = per-thread loads, adds and stores */
+                           buffer fits (default); < 0 = per-thread adds in place */
+    const int *tune_table; /* optional per-Lambda table, tune_entries triples (Lambda_max, k,
+                              n_wrap) with increasing Lambda_max: a grid takes the first entry
+                              with Lambda <= Lambda_max (k as for opts.k; n_wrap != 0); the
+                              library copies it.  NULL / 0 entries: the built-in table.  An
+                              autotuner that measures one is paper_0801_1222_gb300/autotune.py */
+    int tune_entries;
 } hfqmc_opts;
 
 /* Per-grid statistics (hfqmc_get_stats). */

@@ -49,15 +49,19 @@ const TuneEntry kTuneTable[] = {
     {176, 24, 16384}, {1024, 16, 16384},
 };
 
-void tune_lookup(int L, int* k, int* n_wrap) {
-  for (const auto& e : kTuneTable)
-    if (L <= e.L_max) {
-      *k = e.k;
-      *n_wrap = e.n_wrap;
+// k and N_wrap for Lambda from a table (the caller's if non-empty, else the
+// built-in one); beyond its last entry the last entry applies
+void tune_lookup(int L, const std::vector<TuneEntry>& user, int* k, int* n_wrap) {
+  const TuneEntry* t = user.empty() ? kTuneTable : user.data();
+  const size_t n = user.empty() ? sizeof(kTuneTable) / sizeof(kTuneTable[0]) : user.size();
+  for (size_t i = 0; i < n; ++i)
+    if (L <= t[i].L_max) {
+      *k = t[i].k;
+      *n_wrap = t[i].n_wrap;
       return;
     }
-  *k = 64;
-  *n_wrap = 8192;
+  *k = t[n - 1].k;
+  *n_wrap = t[n - 1].n_wrap;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -214,6 +218,18 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     return fail(nullptr, HFQMC_EINVAL, "unknown accept_rule");
   if (o.k != 0 && (o.k < 8 || o.k > 64 || o.k % 8 != 0))
     return fail(nullptr, HFQMC_EINVAL, "k must be 0 or a multiple of 8 in [8, 64]");
+  std::vector<TuneEntry> user_table;
+  if (o.tune_entries < 0 || (o.tune_entries > 0 && !o.tune_table))
+    return fail(nullptr, HFQMC_EINVAL, "tune_table is NULL or tune_entries < 0");
+  for (int i = 0; i < o.tune_entries; ++i) {
+    const TuneEntry e{o.tune_table[3 * i], o.tune_table[3 * i + 1], o.tune_table[3 * i + 2]};
+    if (e.L_max < 1 || e.k < 8 || e.k > 64 || e.k % 8 != 0 || e.n_wrap == 0 ||
+        (i > 0 && e.L_max <= user_table.back().L_max))
+      return fail(nullptr, HFQMC_EINVAL,
+                  "tune_table entry " + std::to_string(i) +
+                      ": needs Lambda_max >= 1 increasing, k a multiple of 8 in [8, 64], n_wrap != 0");
+    user_table.push_back(e);
+  }
 
   std::vector<GridHost> gh(n_grids);
   long long items = 0;
@@ -280,7 +296,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   for (int g = 0; g < n_grids; ++g) {
     GridHost& h = c->gh[g];
     int k_t = 16, nw_t = 1024;
-    tune_lookup(h.L, &k_t, &nw_t);
+    if (o.autotune) tune_lookup(h.L, user_table, &k_t, &nw_t);
     h.k = (o.precision == HFQMC_F32_DELAYED) ? (o.k ? o.k : k_t) : 1;
     h.n_wrap = o.n_wrap ? o.n_wrap : nw_t;
     size_t sm;

@@ -45,7 +45,8 @@ class hfqmc_opts(ctypes.Structure):
                 ("drift_fail", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("autotune", ctypes.c_int), ("flush", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("resident_kb", ctypes.c_int), ("gj_smem", ctypes.c_int), ("gtile", ctypes.c_int)]
+                ("resident_kb", ctypes.c_int), ("gj_smem", ctypes.c_int), ("gtile", ctypes.c_int),
+                ("tune_table", ctypes.POINTER(ctypes.c_int)), ("tune_entries", ctypes.c_int)]
 
 
 class hfqmc_stats(ctypes.Structure):
@@ -243,7 +244,7 @@ class HFQMC:
     def __init__(self, beta, U, dtau, chains_per_grid, seed=1, precision="f32_delayed", k=0,
                  n_wrap=0, accept_rule="metropolis", drift_fail=1e-3, flush="auto",
                  use_graph=True, stream=None, torch_alloc=True, resident_kb=0, gj_smem=0,
-                 gtile=0):
+                 gtile=0, tune=None, autotune=True):
         o = hfqmc_default_opts()
         o.precision = PRECISION[precision]
         o.k = int(k)
@@ -255,6 +256,12 @@ class HFQMC:
         o.resident_kb = int(resident_kb)
         o.gj_smem = int(gj_smem)
         o.gtile = int(gtile)
+        o.autotune = 1 if autotune else 0
+        if tune is not None:  # [(Lambda_max, k, n_wrap), ...] (see autotune.py)
+            flat = [int(v) for e in tune for v in e]
+            self._tune = (ctypes.c_int * len(flat))(*flat)
+            o.tune_table = ctypes.cast(self._tune, ctypes.POINTER(ctypes.c_int))
+            o.tune_entries = len(flat) // 3
         self._allocator = None
         try:
             import torch
