@@ -189,7 +189,11 @@ def run_reference(args, rank, world):
             "unit": "proposals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "beta": beta,
-                                            "grids_L": [g[2] for g in grids]},
+                                            "U": sorted({g[0] for g in grids}),
+                                            "grids_L": [g[2] for g in grids],
+                                            "chains": [g[3] for g in grids],
+                                            "sweeps_per_step": args.sweeps,
+                                            "parallelism": "host cores (bounded sample, see cpu_baseline)"},
             "cpu_baseline": {**cb, "value": value},
             "e2e": {"value": value, "unit": "proposals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
