@@ -88,6 +88,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     int8_t* ss = reinterpret_cast<int8_t*>(smem + lay.off_s);
     unsigned char* stage = smem + lay.off_stage;
     const int KP = lay.KP;
+    const int panel_floats4 = (del_spin_stride(L, KP) + L * KP) / 4;  // one panel, both spins
+    auto zero_panels = [&]() {
+      for (int e = tid; e < 2 * panel_floats4; e += NT)
+        reinterpret_cast<float4*>(e < panel_floats4 ? Pu : Pw)[e < panel_floats4 ? e : e - panel_floats4] =
+            make_float4(0.f, 0.f, 0.f, 0.f);
+    };
     const float d0 = gc.deltaf[0], d1 = gc.deltaf[1];
     const int rule = a.accept_rule;
 
@@ -127,6 +133,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       dg[qq] = 0.f;
     }
     load_diag();
+    zero_panels();
 
     const ChainCounters c0 = *ip.cnt;
     long long n_acc = c0.accepted;
@@ -152,6 +159,9 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       __syncthreads();
       load_diag();
       j = 0;
+      // the panels restart from zeros, so the dot products may run over whole
+      // 16-byte chunks past column j
+      zero_panels();
       __syncthreads();
     };
 
@@ -247,7 +257,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           const float4* Wl = reinterpret_cast<const float4*>(Ws + ol);
           const float4* Ul = reinterpret_cast<const float4*>(Us + ol);
           const float4* Wi = reinterpret_cast<const float4*>(Ws + oi);
-          const int j4 = j >> 2;
+          const int j4 = (j + 3) >> 2;
           for (int m4 = 0; m4 < j4; ++m4) {
             const float4 a1 = Ui[m4], b1 = Wl[m4], a2 = Ul[m4], b2 = Wi[m4];
             c4[0] = __fmaf_rn(a1.x, b1.x, c4[0]);
@@ -258,10 +268,6 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             r4[1] = __fmaf_rn(a2.y, b2.y, r4[1]);
             r4[2] = __fmaf_rn(a2.z, b2.z, r4[2]);
             r4[3] = __fmaf_rn(a2.w, b2.w, r4[3]);
-          }
-          for (int m = 4 * j4; m < j; ++m) {
-            c4[0] = __fmaf_rn(Us[oi + m], Ws[ol + m], c4[0]);
-            r4[0] = __fmaf_rn(Us[ol + m], Ws[oi + m], r4[0]);
           }
           const float uu = gil + ((c4[0] + c4[1]) + (c4[2] + c4[3])) - ((i == l) ? 1.f : 0.f);
           const float ww = (gli + ((r4[0] + r4[1]) + (r4[2] + r4[3]))) * f;
@@ -310,6 +316,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           }
           drift = fmax(drift, d);
           ++n_rec;
+          zero_panels();  // the recompute's workspace may have overlaid them
           load_diag();
           __syncthreads();
         }
@@ -341,6 +348,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
           if (sp == 0 && row0 + qq * kRowStride < L) v += (1.f - dg[qq]) * (1.f - other);
         }
+        __syncthreads();  // every thread has read its totals
+        for (int e = tid; e < 2 * L; e += NT) gsum[e] = 0.f;
         v = block_sum_f(v, reinterpret_cast<float*>(red));
         if (tid == 0) {
           ip.accD[0] += (double)v / (double)L;
