@@ -19,7 +19,7 @@
 
 namespace hfq {
 
-constexpr int kDelNT = 256;          // threads per CTA (8 warps)
+constexpr int kDelNT = 512;          // threads per CTA (16 warps)
 constexpr int kUBlk = 2;             // U blocks of 128 rows staged (and multiplied) together
 constexpr int kTmemCols = 128 * kUBlk; // TMEM columns per CTA: one accumulator per staged U block
 constexpr int kTileN = 128;          // output tile: 128 rows x 128 columns
@@ -420,7 +420,9 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   unsigned char* Whi = stage;
   unsigned char* Wlo = stage + tile_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32*quarter.., columns 64*half..
+  // TMEM lanes 32*quarter.. (the lanes a warp may read); the kDelNT/128 warps of a
+  // quarter split the tile's columns (G rows) into groups, group index `half`
+  const int quarter = warp & 3, half = warp >> 2;
   const int m = 32 * quarter + lane;               // G column nb + m of a tile
   int nhalf = 0;                                   // half tiles handed to the TMA unit
   for (int sp = 0; sp < 2; ++sp) {
@@ -474,8 +476,8 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
               if (threadIdx.x == 0) bulk_wait_read1();
               __syncthreads();
 #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                const int cb = r0 + 32 * half + 16 * c;
+              for (int c = 0; c < 4 / (kDelNT / 128); ++c) {
+                const int cb = r0 + (64 / (kDelNT / 128)) * half + 16 * c;
                 if (cb < N16) {  // warp-uniform
                   float v[16];
                   tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(u * kTileN + cb), v);
@@ -495,8 +497,8 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
             }
           } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int cb = 64 * half + 16 * c;
+            for (int c = 0; c < 8 / (kDelNT / 128); ++c) {
+              const int cb = (128 / (kDelNT / 128)) * half + 16 * c;
               if (cb < N16) {  // warp-uniform: tcgen05.ld is issued by whole warps
                 float v[16];
                 tmem_ld16(tc->tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(u * kTileN + cb), v);

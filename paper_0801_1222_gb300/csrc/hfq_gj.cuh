@@ -27,11 +27,15 @@ namespace hfq {
 // latency is long on this part) whether W lives in shared memory or in L2.
 // On return the right half holds A^{-1} B.  Returns -1 on a zero pivot
 // (uniformly in all threads), 0 otherwise.
-constexpr int kGjChunk = 8;
+// columns per lane and chunk: 8 with 8 warps; 4 with 16 warps, whose register
+// budget is half as large (and twice the warps keep as many loads in flight)
+template <int NT>
+__host__ __device__ constexpr int gj_chunk() { return NT >= 512 ? 4 : 8; }
 
 template <int NT>
 __device__ int gj_eliminate(double* W, int L, double* red, int* redi, double* s_inv, int* s_piv,
                             double* colk) {
+  constexpr int kGjChunk = gj_chunk<NT>();
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ld = 2 * L;
@@ -191,6 +195,7 @@ __device__ double recompute_green(const GridConst& gc, const int8_t* s, T* Gup, 
 template <int NT>
 __device__ int gj_invert_inplace(double* B, int L, double* red, int* redi, double* s_inv, int* s_piv,
                                  double* colk, int* perm) {
+  constexpr int kGjChunk = gj_chunk<NT>();
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ld = L;

@@ -14,7 +14,7 @@
 // The panels are also flushed before every measurement and every FP64
 // recompute (every n_wrap accepted flips).
 //
-// Work split: thread t owns spin (t & 1) of rows r = t/2 + 128 q.  For its
+// Work split (16 warps): thread t owns spin (t & 1) of rows r = t/2 + 256 q.  For its
 // rows it appends the panel entries, keeps the current diagonal G_cur[r][r]
 // in registers, swaps it with its partner thread (the other spin) by one
 // shuffle, and right away evaluates slice r as the next proposal (flip ratio
@@ -31,7 +31,7 @@ namespace hfq {
 
 static_assert(kTileN == kDelayedTile, "tensor-map box and flush tile must agree");
 
-constexpr int kRowsPerThread = 4;  // rows t/2 + 128 q, q < 4: L <= 512
+constexpr int kRowsPerThread = 2;  // rows t/2 + 256 q, q < 2: L <= 512
 constexpr int kRowStride = kDelNT / 2;
 constexpr int kNoSlice = 0x7fffffff;
 
