@@ -28,8 +28,11 @@ struct DelLayout {
   int ldS;      // row pitch of shared-memory G (floats)
   int KP;       // row pitch of the FP32 panels (floats)
   int K8;       // k rounded up to 8 (tf32 MMA K step)
-  // head (kept through a recompute): colk, u, s; body: stage, G, panels, diag
-  size_t off_colk, off_u, off_perm, off_s, off_body;
+  // head: s (and, when the recompute works in shared memory, its scratch colk
+  // and perm, which must survive the workspace overlaying the body; otherwise
+  // they live in the idle staging area); body: stage, G, panels, diag
+  size_t off_colk, off_perm, off_s, off_body;
+  int ub;       // U blocks staged (and multiplied) together by the flush
   size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
 };
 
@@ -48,38 +51,50 @@ __host__ __device__ inline int del_spin_stride(int L, int KP) {
   return L * KP + ((16 - (L * KP) % 32) + 32) % 32;
 }
 
-// stage: W hi, W lo (one block of 128 rows), then U hi, U lo for up to kUBlk
-// blocks (as many as L has), tf32 in core-matrix layout, 128 x K8 each
-__host__ __device__ inline int del_ublocks(int L) {
+// stage: W hi, W lo (one block of 128 rows), then U hi, U lo for ub U blocks
+// (at most kUBlk and at most as many as L has), tf32 in core-matrix layout,
+// 128 x K8 each
+__host__ __device__ inline int del_ublocks(int L, int ub) {
   const int lb = (L + 127) / 128;
-  return lb < kUBlk ? lb : kUBlk;
+  const int u = ub < kUBlk ? ub : kUBlk;
+  return lb < u ? lb : u;
 }
-__host__ __device__ inline size_t del_stage_bytes(int K, int L) {
+__host__ __device__ inline size_t del_stage_bytes(int K, int L, int ub) {
   const int K8 = (K + 7) / 8 * 8;
-  return (size_t)(2 + 2 * del_ublocks(L)) * kTileN * K8 * 4;
+  return (size_t)(2 + 2 * del_ublocks(L, ub)) * kTileN * K8 * 4;
 }
 
 __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem,
-                                                bool gtile = false) {
+                                                bool gtile = false, int ub = kUBlk) {
   DelLayout d;
   d.ldS = L | 1;
   d.KP = K + 4;  // 16-byte rows; (K+4) mod 32 spreads 8 rows of a 16-byte load over all banks
   d.K8 = (K + 7) / 8 * 8;
+  d.ub = del_ublocks(L, ub);
   size_t o = 0;
-  d.off_colk = o;
-  o += del_align((size_t)L * 8, 128);
-  d.off_u = o;
-  o += del_align((size_t)L * 4, 128);
-  d.off_perm = o;
-  o += del_align((size_t)L * 4, 128);
+  if (gj_smem) {
+    d.off_colk = o;
+    o += del_align((size_t)L * 8, 128);
+    d.off_perm = o;
+    o += del_align((size_t)L * 4, 128);
+  }
   d.off_s = o;
   o += del_align((size_t)L, 128);
   o = del_align(o, 1024);
   d.off_body = o;
   d.off_stage = o;
-  // the staging area doubles as the measurement's per-warp partial sums
+  if (!gj_smem) {  // the recompute's scratch in the (then idle) staging area
+    d.off_colk = o;
+    d.off_perm = o + del_align((size_t)L * 8, 128);
+  }
+  // the staging area doubles as the measurement's per-warp partial sums and
+  // holds the recompute's scratch when that is not in the head
   const size_t part = 2 * (size_t)(kDelNT / 32) * L * 4;
-  o += del_align(del_stage_bytes(K, L) > part ? del_stage_bytes(K, L) : part, 1024);
+  const size_t scratch = del_align((size_t)L * 8, 128) + del_align((size_t)L * 4, 128);
+  size_t st = del_stage_bytes(K, L, ub);
+  if (part > st) st = part;
+  if (scratch > st) st = scratch;
+  o += del_align(st, 1024);
   d.off_G = o;
   if (resident) o += del_align(2 * (size_t)L * d.ldS * 4, 128);
   d.off_U = o;
@@ -416,7 +431,7 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   const int K8 = (j + 7) / 8 * 8;
   const size_t tile_bytes = (size_t)kTileN * lay.K8 * 4;
   const int LB = (L + kTileN - 1) / kTileN;  // blocks of 128 rows / columns
-  const int UB = del_ublocks(L);             // U blocks staged together
+  const int UB = lay.ub;                     // U blocks staged together
   unsigned char* Whi = stage;
   unsigned char* Wlo = stage + tile_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -36,6 +36,7 @@ struct GridConst {
   int n_wrap;      // recompute interval in accepted flips (<= 0: never)
   int gj_smem;     // 1: the FP64 recompute works in shared memory
   int gtile;       // 1: the delayed flush adds its tiles to G by TMA reduce (tmapG)
+  int ub;          // U blocks staged together by the delayed flush (1 or 2)
   double lambda;   // cosh(lambda) = exp(dtau U / 2)
   double delta[2]; // Delta for sigma*s = +1: e^{-2 lambda} - 1; sigma*s = -1: e^{2 lambda} - 1
   double dV[2];    // e^{sigma lambda s} - 1 for sigma*s = +1 / -1

@@ -32,7 +32,7 @@ thread_local std::string g_create_error;
 
 struct GridHost {
   double U, dtau, lambda;
-  int L, chains, item0, k, n_wrap, resident, gj_smem, gtile = 0;
+  int L, chains, item0, k, n_wrap, resident, gj_smem, gtile = 0, ub = 2;
   bool g0_set = false, ever_set = false;
   long long out_off;
 };
@@ -290,7 +290,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   size_t smem_max = 0;
   const size_t kResidentBudget =
       o.resident_kb == 0 ? 200 * 1024 : (o.resident_kb < 0 ? 0 : (size_t)o.resident_kb * 1024);
-  const size_t kSmemMax = 227 * 1024;
+  const size_t kSmemMax = 227 * 1024 - 512;  // dynamic; the rest is the static shared memory
   c->gc.resize(n_grids);
   long long out_off = 0;
   for (int g = 0; g < n_grids; ++g) {
@@ -309,29 +309,35 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
         return HFQMC_EINVAL;
       }
       // the panels of both spins must fit in shared memory: lower k if needed
-      while (h.k > 8 && delayed_smem(h.L, h.k, false, h.gj_smem) > kSmemMax) h.k -= 8;
-      if (delayed_smem(h.L, h.k, false, h.gj_smem) > kSmemMax) {
+      while (h.k > 8 && delayed_smem(h.L, h.k, false, h.gj_smem, false, 1) > kSmemMax) h.k -= 8;
+      if (delayed_smem(h.L, h.k, false, h.gj_smem, false, 1) > kSmemMax) {
         g_create_error = "Lambda too large for the delayed path's shared-memory panels";
         hfqmc_destroy(c);
         return HFQMC_EINVAL;
       }
-      sm = delayed_smem(h.L, h.k, true, h.gj_smem);
+      // staging two U blocks per flush group when it fits, else one
+      h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2) <= kSmemMax ? 2 : 1;
+      sm = delayed_smem(h.L, h.k, true, h.gj_smem, false, h.ub);
       h.resident = sm <= kResidentBudget;
       h.gtile = 0;
       if (!h.resident) {
         // flush by TMA reduce-add: G rows must be 16-byte aligned (Lambda % 4
         // == 0), the 64 KiB product buffers must fit (k is lowered for them
-        // down to 8), the driver must encode the tensor map
+        // down to 8; at each k two staged U blocks are preferred, one
+        // accepted), the driver must encode the tensor map
         if (o.flush != HFQMC_FLUSH_FFMA && h.L % 4 == 0 && o.gtile >= 0 &&
             tensor_map_encoder() != nullptr) {
-          int kt = h.k;
-          while (kt > 8 && delayed_smem(h.L, kt, false, h.gj_smem, true) > kSmemMax) kt -= 8;
-          if (delayed_smem(h.L, kt, false, h.gj_smem, true) <= kSmemMax) {
-            h.k = kt;
-            h.gtile = 1;
-          }
+          for (int kt = h.k; kt >= 8 && !h.gtile; kt -= 8)
+            for (int ub = 2; ub >= 1 && !h.gtile; --ub)
+              if (delayed_smem(h.L, kt, false, h.gj_smem, true, ub) <= kSmemMax) {
+                h.k = kt;
+                h.ub = ub;
+                h.gtile = 1;
+              }
         }
-        sm = delayed_smem(h.L, h.k, false, h.gj_smem, h.gtile != 0);
+        if (!h.gtile)
+          h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2) <= kSmemMax ? 2 : 1;
+        sm = delayed_smem(h.L, h.k, false, h.gj_smem, h.gtile != 0, h.ub);
       }
     } else {
       sm = rank1_smem(h.L, true, f64, h.gj_smem);
@@ -350,6 +356,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     q.n_wrap = h.n_wrap;
     q.gj_smem = h.gj_smem;
     q.gtile = h.gtile;
+    q.ub = h.ub;
     q.lambda = h.lambda;
     q.delta[0] = std::exp(-2.0 * h.lambda) - 1.0;
     q.delta[1] = std::exp(2.0 * h.lambda) - 1.0;

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     const GridConst gc = a.grids[ip.grid];
     const int L = gc.L, K = gc.k;
     const bool resident = gc.resident != 0;
-    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0);
+    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0, gc.ub);
     // product tile buffer of the TMA reduce flush (G in HBM, tensor map set)
     float* dtile = gc.gtile ? reinterpret_cast<float*>(smem + lay.off_gtile) : nullptr;
 
@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   if (use_tc) tc_teardown(&tc);
 }
 
-size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile) {
-  return del_layout(L, k, resident, gj_smem, gtile).bytes;
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int ub) {
+  return del_layout(L, k, resident, gj_smem, gtile, ub).bytes;
 }
 
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
