@@ -89,8 +89,10 @@ typedef struct {
     void *alloc_user;
     int resident_kb;    /* shared-memory budget (KiB per CTA) for keeping a chain's G on chip:
                            0 = default (200), < 0 = never (G stays in HBM/L2) */
-    int gj_smem;        /* FP64 recompute in shared memory when its Lambda x Lambda workspace fits (Lambda <= 168):
-                           0 = yes, < 0 = never (HBM workspace; lower shared-memory footprint) */
+    int gj_smem;        /* rank-1 paths and initialisation: FP64 recompute in shared memory when its
+                           Lambda x Lambda workspace fits (Lambda <= 168): 0 = yes, < 0 = never (HBM
+                           workspace, inverted by 16-column panels when their scratch fits).  The FP32
+                           delayed path always inverts its HBM workspace by panels. */
     int gtile;          /* delayed flush with G in HBM: >= 0 = add each 128x128 product tile to G
                            by one TMA tensor reduce-add when Lambda % 4 == 0 and the 64 KiB tile
                            buffer fits (default); < 0 = per-thread adds in place */

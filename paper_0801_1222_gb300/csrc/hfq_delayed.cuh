@@ -34,6 +34,7 @@ struct DelLayout {
   size_t off_colk, off_perm, off_s, off_body;
   int ub;       // U blocks staged (and multiplied) together by the flush
   size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
+  size_t off_gjb;  // the recompute's panel scratch (workspace in HBM), overlaying all but G
 };
 
 // product buffers of the TMA reduce flush: two halves of a tile, 64 rows x
@@ -110,6 +111,10 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
     o += kGTileBytes;
   }
   if (gj_smem && d.off_body + gj_smem_bytes(L) > o) o = d.off_body + gj_smem_bytes(L);
+  // the blocked recompute's scratch: after colk and perm, or after G when
+  // G is resident (with the workspace in shared memory it is not used)
+  d.off_gjb = resident ? del_align(d.off_U, 128) : del_align(d.off_body + scratch, 128);
+  if (!gj_smem && d.off_gjb + gj_blocked_bytes(L) > o) o = d.off_gjb + gj_blocked_bytes(L);
   d.bytes = o;
   return d;
 }

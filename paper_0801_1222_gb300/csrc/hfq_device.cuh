@@ -98,6 +98,18 @@ struct SweepArgs {
 // Bytes of shared memory the FP64 recompute needs for its L x L workspace.
 __host__ __device__ inline size_t gj_smem_bytes(int L) { return (size_t)L * L * sizeof(double); }
 
+// Pivot columns per panel of the blocked FP64 inversion (workspace in HBM)
+// and the shared scratch it needs: the L x kGjPanel panel (pitch kGjPanel + 1)
+// and the panel's pivot rows (kGjPanel x L).
+constexpr int kGjPanel = 16;
+__host__ __device__ inline size_t gj_blocked_bytes(int L) {
+  return ((size_t)L * (kGjPanel + 1) + (size_t)kGjPanel * L) * sizeof(double);
+}
+
+// Dynamic shared memory a kernel may request (the rest of the SM's 227 KB
+// holds the static shared memory).
+constexpr size_t kSmemCap = 227 * 1024 - 512;
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
 // 32x32 -> 64-bit products of counter words 0 and 2 with the round

@@ -10,9 +10,14 @@
 //  * recompute_green: on the augmented L x 2L matrix [A | M], 1.5 L^3 DFMA
 //    per spin.  Used by the entry point that allocates nothing.
 //  * recompute_green_inv: G = B^{-1} with B = M^{-1}(1 + D) - D inverted in
-//    place, L^3 DFMA per spin on an L x L workspace -- shared memory when it
-//    fits (Lambda <= 168), the chain's HBM workspace otherwise (L2-resident
-//    for the sizes used).  Used by every sweep kernel and the initialisation.
+//    place, L^3 DFMA per spin on an L x L workspace.  Used by every sweep
+//    kernel and the initialisation.  Two forms of the inversion:
+//    gj_invert_inplace (row interchanges) on a workspace in shared memory
+//    (rank-1 paths and initialisation, Lambda <= 168) or in HBM when nothing
+//    else fits; gj_invert_blocked (implicit pivoting, kGjPanel columns per
+//    panel in shared memory) on the chain's HBM workspace, which it reads and
+//    writes once per panel instead of once per pivot column -- the FP32
+//    delayed path always, the initialisation whenever the panel fits.
 #pragma once
 #include "hfq_device.cuh"
 
@@ -310,15 +315,174 @@ __device__ int gj_invert_inplace(double* B, int L, double* red, int* redi, doubl
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Blocked form of the same inversion for a workspace in HBM.  Rows are never
+// interchanged (implicit pivoting): step k takes as pivot p_k the row of
+// largest |B_ik| among the rows not yet used (ties: lowest index), scales row
+// p_k and eliminates column k from every other row, the identity column
+// folded in as above.  Relabelling row p_k as row k makes this the unpivoted
+// in-place inversion of P B, whose result is (P B)^{-1} = B^{-1} P^T; with
+// pos(p_k) = k the inverse is
+//   (B^{-1})_{km} = B'_{p_k, pos(m)}           (B' the array on return),
+// applied by the caller while it copies the result out.
+//
+// The pivot columns are taken kGjPanel at a time.  A panel (all L rows of
+// columns k0 .. k0 + b - 1) is reduced in shared memory by the b steps; for
+// every other column x the b steps compose to
+//   x <- x + (V - E) x_P,
+// V the reduced panel, P the panel's pivot rows and E their unit rows (a
+// product of the steps' rank-1 maps, each x <- x + (v_k - e_{p_k}) x_{p_k}),
+// so the rest of B takes one rank-b update per panel: its rows p in P are
+// replaced by V_p x_P and the other rows i get x_i + V_i x_P.  B is read and
+// written once per panel (L^3 / b words in all) instead of once per pivot
+// column (L^3), and the update runs from registers at the FP64 pipe's rate.
+// pan: gj_blocked_bytes(L) of shared scratch (the panel, pitch kGjPanel + 1,
+// then the pivot rows' slab, pitch L); perm, pos: L ints each of shared
+// memory (pivot row of step k; step of row i).  Returns -1 on a zero pivot
+// (uniformly in all threads), 0 otherwise.
+// ---------------------------------------------------------------------------
+
+template <int NT>
+__device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, double* s_inv, int* s_piv,
+                                 int* perm, int* pos, double* pan) {
+  constexpr int NW = NT / 32;
+  constexpr int KB = kGjPanel, PP = KB + 1;  // odd pitch: a column of the panel is conflict-free
+  constexpr int TR = 8;                      // rows of an update item (one warp, 32 columns)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* slab = pan + (size_t)L * PP;
+  for (int i = tid; i < L; i += NT) pos[i] = -1;
+  __syncthreads();
+  for (int k0 = 0; k0 < L; k0 += KB) {
+    const int bb = min(KB, L - k0);
+    for (int i = warp; i < L; i += NW)
+      if (lane < bb) pan[i * PP + lane] = B[(size_t)i * L + k0 + lane];
+    __syncthreads();
+    for (int t = 0; t < bb; ++t) {
+      const int k = k0 + t;
+      double best = -1.0;
+      int bi = L;
+      for (int i = tid; i < L; i += NT)
+        if (pos[i] < 0) {
+          const double v = fabs(pan[i * PP + t]);
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
+      for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        red[warp] = best;
+        redi[warp] = bi;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // the warps' candidates (largest |pivot|, then lowest row), the
+        // reciprocal, and the pivot row scaled (its column-t entry becomes
+        // the reciprocal) into the slab's first KB words, which the update
+        // overwrites later; the panel's copy is replaced after the barrier
+        best = lane < NW ? red[lane] : -1.0;
+        bi = lane < NW ? redi[lane] : L;
+        for (int o = 16; o; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+          }
+        }
+        const bool ok = best > 0.0 && bi < L;
+        const double inv = ok ? 1.0 / pan[bi * PP + t] : 0.0;
+        if (ok && lane < bb) slab[lane] = (lane == t) ? inv : pan[bi * PP + lane] * inv;
+        if (lane == 0) {
+          *s_piv = ok ? bi : -1;
+          *s_inv = inv;
+          if (ok) {
+            perm[k] = bi;
+            pos[bi] = k;
+          }
+        }
+      }
+      __syncthreads();
+      const int p = *s_piv;
+      if (p < 0) return -1;
+      const double inv = *s_inv;
+      for (int i = tid; i < L; i += NT) {
+        double* pr = pan + i * PP;
+        if (i == p) {
+#pragma unroll
+          for (int u = 0; u < KB; ++u)
+            if (u < bb) pr[u] = slab[u];
+          continue;
+        }
+        const double c = pr[t];
+#pragma unroll
+        for (int u = 0; u < KB; ++u)
+          if (u < bb && u != t) pr[u] = fma(-c, slab[u], pr[u]);
+        pr[t] = -c * inv;
+      }
+      __syncthreads();
+    }
+    // the pivot rows of the other columns, then their rank-b update, in
+    // items of TR rows x 32 columns spread over the warps; the nR other
+    // columns are numbered c = 0 .. nR - 1 around the panel
+    const int* pk = perm + k0;
+    for (int e = tid; e < bb * L; e += NT) {
+      const int t = e / L, j = e - t * L;
+      slab[e] = B[(size_t)pk[t] * L + j];
+    }
+    __syncthreads();
+    const int nR = L - bb;
+    const int ncg = (nR + 31) / 32, nrb = (L + TR - 1) / TR;
+    for (int it = warp; it < ncg * nrb; it += NW) {
+      const int cg = it % ncg, r0 = (it / ncg) * TR;
+      const int c = cg * 32 + lane;
+      const bool jin = c < nR;
+      const int j = c < k0 ? c : c + bb;
+      double acc[TR];
+#pragma unroll
+      for (int q = 0; q < TR; ++q) {
+        const int i = r0 + q;
+        const bool piv = i < L && pos[i] >= k0 && pos[i] < k0 + bb;
+        acc[q] = (jin && i < L && !piv) ? B[(size_t)i * L + j] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        if (t < bb) {
+          const double sv = jin ? slab[t * L + j] : 0.0;
+#pragma unroll
+          for (int q = 0; q < TR; ++q)
+            if (r0 + q < L) acc[q] = fma(pan[(r0 + q) * PP + t], sv, acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TR; ++q)
+        if (jin && r0 + q < L) B[(size_t)(r0 + q) * L + j] = acc[q];
+    }
+    for (int i = warp; i < L; i += NW)
+      if (lane < bb) B[(size_t)i * L + k0 + lane] = pan[i * PP + lane];
+    __syncthreads();
+  }
+  return 0;
+}
+
 // Recomputes G^up and G^dn through the inverse (see above); [sp_lo, sp_hi)
 // selects the spins (0: up, 1: down).  W: L x L FP64
-// workspace; colk: L doubles and perm: L ints of shared scratch.  Returns the
-// drift max |G_old - G_new| when with_drift, 0 otherwise, -1 after a zero pivot.
-template <typename T, int NT>
+// workspace; colk: L doubles and perm: L ints of shared scratch.  kBlocked:
+// inverted by panels, pan being gj_blocked_bytes(L) of shared scratch (colk
+// then holds the row positions).  Returns the drift max |G_old - G_new| when
+// with_drift, 0 otherwise, -1 after a zero pivot.
+template <typename T, int NT, bool kBlocked = false>
 __device__ double recompute_green_inv(const GridConst& gc, const int8_t* s, T* Gup, T* Gdn, int ldG,
                                       double* W, double* red, int* redi, double* s_inv, int* s_piv,
                                       double* colk, int* perm, bool with_drift, int* status_word,
-                                      int sp_lo = 0, int sp_hi = 2) {
+                                      int sp_lo = 0, int sp_hi = 2, double* pan = nullptr) {
   constexpr int NW = NT / 32;
   const int L = gc.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -339,17 +503,26 @@ __device__ double recompute_green_inv(const GridConst& gc, const int8_t* s, T* G
         }
       }
       __syncthreads();
-      if (gj_invert_inplace<NT>(W, L, red, redi, s_inv, s_piv, colk, perm) != 0) {
+      int rc;
+      if constexpr (kBlocked)
+        rc = gj_invert_blocked<NT>(W, L, red, redi, s_inv, s_piv, perm, reinterpret_cast<int*>(colk), pan);
+      else
+        rc = gj_invert_inplace<NT>(W, L, red, redi, s_inv, s_piv, colk, perm);
+      if (rc != 0) {
         if (tid == 0) atomicOr(status_word, kStatusSingular);
         return -1.0;
       }
       src = W;
     }
+    // the blocked inversion leaves row p_k of the inverse at row perm[k] and
+    // its column m at column pos[m]
+    const bool implicit = kBlocked && !free_bath;
+    const int* pos = reinterpret_cast<const int*>(colk);
     for (int i = warp; i < L; i += NW) {
-      const double* Si = src + (size_t)i * L;
+      const double* Si = src + (size_t)(implicit ? perm[i] : i) * L;
       T* Gi = G + (size_t)i * ldG;
       for (int j = lane; j < L; j += 32) {
-        const double gn = Si[j];
+        const double gn = Si[implicit ? pos[j] : j];
         if (with_drift) dmax = fmax(dmax, fabs((double)Gi[j] - gn));
         finite = finite && isfinite(gn);
         Gi[j] = (T)gn;

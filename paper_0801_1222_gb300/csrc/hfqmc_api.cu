@@ -290,7 +290,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   size_t smem_max = 0;
   const size_t kResidentBudget =
       o.resident_kb == 0 ? 200 * 1024 : (o.resident_kb < 0 ? 0 : (size_t)o.resident_kb * 1024);
-  const size_t kSmemMax = 227 * 1024 - 512;  // dynamic; the rest is the static shared memory
+  const size_t kSmemMax = kSmemCap;
   c->gc.resize(n_grids);
   long long out_off = 0;
   for (int g = 0; g < n_grids; ++g) {
@@ -300,8 +300,10 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     h.k = (o.precision == HFQMC_F32_DELAYED) ? (o.k ? o.k : k_t) : 1;
     h.n_wrap = o.n_wrap ? o.n_wrap : nw_t;
     size_t sm;
-    // the FP64 recompute works in shared memory when its workspace fits next to the head
-    h.gj_smem = o.gj_smem >= 0 && gj_smem_bytes(h.L) + 4 * (size_t)h.L * 8 + 1024 <= kSmemMax;
+    // the FP64 recompute works in shared memory when its workspace fits next to the head;
+    // the delayed path always inverts its HBM workspace by panels
+    h.gj_smem = o.precision != HFQMC_F32_DELAYED && o.gj_smem >= 0 &&
+                gj_smem_bytes(h.L) + 4 * (size_t)h.L * 8 + 1024 <= kSmemMax;
     if (o.precision == HFQMC_F32_DELAYED) {
       if (h.L > 512) {
         g_create_error = "the delayed path handles Lambda <= 512 (two rows per thread)";

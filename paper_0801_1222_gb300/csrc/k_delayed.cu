@@ -294,26 +294,11 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         if (gc.n_wrap > 0 && --until_rec == 0) {
           until_rec = gc.n_wrap;
           flush();
-          double d;
-          if (gc.gj_smem) {
-            // the FP64 workspace overlays the body of shared memory: G goes home to HBM first
-            if (resident) {
-              for (int i = warp; i < 2 * L; i += NW)
-                for (int jj = lane; jj < L; jj += 32) Ggl[(size_t)i * L + jj] = Gu[(size_t)i * ld + jj];
-              __syncthreads();
-            }
-            d = recompute_green_inv<float, NT>(gc, ss, Ggl, Ggl + (size_t)L * L, L,
-                                               reinterpret_cast<double*>(smem + lay.off_body), red,
-                                               redi, &s_inv, &s_piv, colk, perm, true, a.status);
-            if (resident) {
-              for (int i = warp; i < 2 * L; i += NW)
-                for (int jj = lane; jj < L; jj += 32) Gu[(size_t)i * ld + jj] = Ggl[(size_t)i * L + jj];
-              __syncthreads();
-            }
-          } else {
-            d = recompute_green_inv<float, NT>(gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv,
-                                               colk, perm, true, a.status);
-          }
+          // FP64 workspace in HBM, inverted by panels whose scratch overlays
+          // the idle part of shared memory (never G)
+          const double d = recompute_green_inv<float, NT, true>(
+              gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv, colk, perm, true, a.status, 0, 2,
+              reinterpret_cast<double*>(smem + lay.off_gjb));
           drift = fmax(drift, d);
           ++n_rec;
           zero_panels();  // the recompute's workspace may have overlaid them

@@ -26,6 +26,11 @@ int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st) 
 __host__ __device__ inline size_t init_head_bytes(int L) {
   return ((size_t)L * sizeof(double) + (size_t)L * sizeof(int) + (size_t)L + 15) / 16 * 16;
 }
+// with the workspace in HBM: whether the blocked inversion's panel scratch
+// fits after the head
+__host__ __device__ inline bool init_blocked(int L) {
+  return init_head_bytes(L) + gj_blocked_bytes(L) <= kSmemCap;
+}
 
 // M^{-1} of one grid's bath matrix.  M is skew-circulant: M_{ll'} = c(l - l')
 // with c(d) = -G0(tau_d) and c(d - L) = -c(d) (the antiperiodic wrap).  The
@@ -119,6 +124,8 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
   int* perm = reinterpret_cast<int*>(colk + L);
   int8_t* sf = reinterpret_cast<int8_t*>(perm + L);
   double* W = gc.gj_smem ? reinterpret_cast<double*>(dsm + init_head_bytes(L)) : ip.ws + (size_t)sp * L * L;
+  // workspace in HBM: inverted by panels when their scratch fits after the head
+  double* pan = !gc.gj_smem && init_blocked(L) ? reinterpret_cast<double*>(dsm + init_head_bytes(L)) : nullptr;
   // the field: drawn afresh (both blocks draw the same values; the spin-up
   // block stores it) or the chain's current one
   for (int l = tid; l < L; l += NT) {
@@ -128,8 +135,12 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
   }
   __syncthreads();
   T* G = reinterpret_cast<T*>(ip.G);
-  recompute_green_inv<T, NT>(gc, sf, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk, perm,
-                             false, a.status, sp, sp + 1);
+  if (pan)
+    recompute_green_inv<T, NT, true>(gc, sf, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk,
+                                     perm, false, a.status, sp, sp + 1, pan);
+  else
+    recompute_green_inv<T, NT>(gc, sf, G, G + (size_t)L * L, L, W, red, redi, &s_inv, &s_piv, colk, perm,
+                               false, a.status, sp, sp + 1);
   if (sp != 0) return;
   for (int k = tid; k < 2 * L; k += NT) ip.acc[k] = 0.0;
   for (int k = tid; k < kBins * L; k += NT) ip.bins[k] = 0.0;
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
 }
 
 size_t init_smem(int L, bool gj_smem) {
-  return init_head_bytes(L) + (gj_smem ? gj_smem_bytes(L) : 0);
+  return init_head_bytes(L) + (gj_smem ? gj_smem_bytes(L) : (init_blocked(L) ? gj_blocked_bytes(L) : 0));
 }
 
 int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item0, int n_chains,

@@ -56,6 +56,26 @@ def test_uneven_grids_delayed_with_recompute(orc):
                 assert err < 1e-3
 
 
+
+def test_delayed_hbm_recompute_by_panels(orc):
+    """Lambda = 200, recompute every 32 accepted flips: the sweep kernel
+    inverts the FP64 workspace in HBM by panels, with the panel scratch over
+    its idle shared memory.  A wrong inverse would show as an O(1) drift
+    against the FP32 G; the drift stays at the FP32 level of 32 flips, and G
+    follows the oracle wherever the decisions agree."""
+    ctx, q = make_pair(orc, 20.0, [(5.0, 0.1)], [2], precision="f32_delayed", n_wrap=32,
+                       drift_fail=1.0)
+    ctx.sweep(1, 1)
+    q.sweep(1, 1)
+    st = ctx.get_stats(0)
+    assert st["recomputes"] >= 2
+    assert st["drift_max"] < 1e-3
+    for c, och in enumerate(q.chains[0]):
+        gc = ctx.get_chain(0, c)
+        if gc["hash"] == och.decision_hash:
+            err = max(np.abs(gc["Gup"] - och.Gup).max(), np.abs(gc["Gdn"] - och.Gdn).max())
+            assert err < 1e-3
+
 def test_tcgen05_flush_matches_ffma_flush():
     from paper_0801_1222_gb300 import inputs
     h = lib()

@@ -47,6 +47,17 @@ def test_uneven_grids_resident_and_hbm(orc):
         assert np.max(np.abs(ctx.get_G(g)[0] - q.get_G(g)[0])) < 1e-10
 
 
+
+def test_hbm_workspace_blocked_inversion_L200(orc):
+    """Lambda = 200: the FP64 workspace does not fit in shared memory, so the
+    initial G of each chain comes from the inversion by 16-column panels
+    (implicit pivoting); the decisions and G follow the oracle's LU solve to
+    1e-10 over several sweeps with recomputes."""
+    ctx, q = make_pair(orc, 20.0, [(5.0, 0.1)], [2], n_wrap=64)
+    ctx.sweep(1, 2)
+    q.sweep(1, 2)
+    compare_chains(ctx, q)
+
 def test_heat_bath_decisions(orc):
     ctx, q = make_pair(orc, 8.0, [(4.0, 0.25)], [4], accept_rule="heat_bath", n_wrap=16)
     ctx.sweep(20, 100)
