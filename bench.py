@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
-TRAFFIC_PER_1000_SWEEPS = 1.272240640e9 + 52.478109440e9  # dram read + write of one launch (ncu)
+TRAFFIC_PER_1000_SWEEPS = None  # dram read + write of one launch (ncu); unset until recaptured for the current kernel
 
 
 def parse():
@@ -267,7 +267,7 @@ def run_ours(args, rank, world, local):
     achieved = flops_step / (statistics.median(step_ms) * 1e-3) / 1e12
     # DRAM bytes of one full-size launch (1000 sweeps of this workload), from
     # the ncu capture summarised in profiles/k_sweep_delayed_multigrid.md
-    traffic = TRAFFIC_PER_1000_SWEEPS if (args.workload == "multigrid_L100_240" and S == 1000
+    traffic = TRAFFIC_PER_1000_SWEEPS if (TRAFFIC_PER_1000_SWEEPS and args.workload == "multigrid_L100_240" and S == 1000
                                           and args.precision == "f32_delayed" and not args.chains
                                           and not args.k and not args.n_wrap) else None
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
