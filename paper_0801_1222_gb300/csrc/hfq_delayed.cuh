@@ -1,16 +1,20 @@
 // Support of the delayed (rank-k) FP32 sweep: shared-memory layout, FP32
 // flip ratio, and the two flush engines for G += U W^T:
-//   * flush_tcgen05 -- 5th-generation tensor cores.  Per spin and per
-//     128 x 128 output tile: the panels are split into TF32 hi/lo parts in
-//     shared memory (K-major, no swizzle, 8-row x 16-byte core matrices), one
-//     thread issues tcgen05.mma kind::tf32 (M=128, N<=128, K=8 per
-//     instruction) for hi*hi + hi*lo + lo*hi into a TMEM accumulator,
+//   * flush_tcgen05 -- 5th-generation tensor cores.  Per spin the panels are
+//     scaled by powers of two (each panel's largest magnitude to [2^14, 2^15))
+//     and split into FP16 hi/lo parts in shared memory (K-major, no swizzle,
+//     8-row x 16-byte core matrices); per 128 x 128 output tile one thread
+//     issues tcgen05.mma kind::f16 (M=128, N<=128, K=16 per instruction, FP32
+//     accumulation) for hi*hi + hi*lo + lo*hi into a TMEM accumulator,
 //     commits to an mbarrier, and all warps read the tile back with
-//     tcgen05.ld.  With G in HBM the tile goes to a shared-memory buffer and
-//     one TMA tensor reduce-add sends it to G (the addition happens in L2;
-//     the SM never loads G); with G in shared memory the warps add it in
-//     place.  The dropped lo*lo term and the TF32 rounding of lo leave a
-//     relative error ~2^-21 per product.
+//     tcgen05.ld and undo the scaling (exact).  With G in HBM the tile goes to
+//     a shared-memory buffer and one TMA tensor reduce-add sends it to G (the
+//     addition happens in L2; the SM never loads G); with G in shared memory
+//     the warps add it in place.  hi and lo carry 11 significant bits each, as
+//     TF32 would, so the dropped lo*lo term and the rounding of lo leave a
+//     relative error ~2^-21 per product; the scaling keeps every part but
+//     those below 2^-29 of the panel's largest entry out of the FP16
+//     subnormal range, at the FP16 tensor rate (twice TF32's).
 //   * flush_ffma -- FP32 FMA on the CUDA cores (4 x 4 register tiles).
 #pragma once
 #include <cstdint>
@@ -27,7 +31,7 @@ constexpr int kTileN = 128;          // output tile: 128 rows x 128 columns
 struct DelLayout {
   int ldS;      // row pitch of shared-memory G (floats)
   int KP;       // row pitch of the FP32 panels (floats)
-  int K8;       // k rounded up to 8 (tf32 MMA K step)
+  int KS;       // k rounded up to 16 (FP16 MMA K step): K extent of a staged tile
   // head: s (and, when the recompute works in shared memory, its scratch colk
   // and perm, which must survive the workspace overlaying the body; otherwise
   // they live in the idle staging area); body: stage, G, panels, diag
@@ -53,16 +57,16 @@ __host__ __device__ inline int del_spin_stride(int L, int KP) {
 }
 
 // stage: W hi, W lo (one block of 128 rows), then U hi, U lo for ub U blocks
-// (at most kUBlk and at most as many as L has), tf32 in core-matrix layout,
-// 128 x K8 each
+// (at most kUBlk and at most as many as L has), FP16 in core-matrix layout,
+// 128 x KS each
 __host__ __device__ inline int del_ublocks(int L, int ub) {
   const int lb = (L + 127) / 128;
   const int u = ub < kUBlk ? ub : kUBlk;
   return lb < u ? lb : u;
 }
 __host__ __device__ inline size_t del_stage_bytes(int K, int L, int ub) {
-  const int K8 = (K + 7) / 8 * 8;
-  return (size_t)(2 + 2 * del_ublocks(L, ub)) * kTileN * K8 * 4;
+  const int KS = (K + 15) / 16 * 16;
+  return (size_t)(2 + 2 * del_ublocks(L, ub)) * kTileN * KS * 2;
 }
 
 __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem,
@@ -70,7 +74,7 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   DelLayout d;
   d.ldS = L | 1;
   d.KP = K + 4;  // 16-byte rows; (K+4) mod 32 spreads 8 rows of a 16-byte load over all banks
-  d.K8 = (K + 7) / 8 * 8;
+  d.KS = (K + 15) / 16 * 16;
   d.ub = del_ublocks(L, ub);
   size_t o = 0;
   if (gj_smem) {
@@ -198,18 +202,24 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint32_t f32_to_tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// FP32 -> FP16 (round to nearest even) as the 16-bit pattern, and back
+__device__ __forceinline__ uint32_t f32_to_f16_bits(float x) {
+  unsigned short h;
+  asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  return h;
+}
+__device__ __forceinline__ float f16_bits_to_f32(uint32_t h) {
+  float x;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(x) : "h"((unsigned short)h));
+  return x;
 }
 
-// K-major, no-swizzle canonical layout: element (r, m) of a rows x K8 tile
-// lives at (r/8)*SBO + (m/4)*LBO + (r%8)*16 + (m%4)*4 bytes, with the
+// K-major, no-swizzle canonical layout: element (r, m) of a rows x KS FP16
+// tile lives at (r/8)*SBO + (m/8)*LBO + (r%8)*16 + (m%8)*2 bytes, with the
 // 8-row x 16-byte core matrices contiguous along K (LBO = 128 B) and the
-// 8-row groups SBO = (K8/4)*128 B apart.
-__device__ __forceinline__ uint32_t core_offset(int r, int m, int K8) {
-  return (uint32_t)((r >> 3) * (K8 / 4) * 128 + (m >> 2) * 128 + (r & 7) * 16 + (m & 3) * 4);
+// 8-row groups SBO = (KS/8)*128 B apart.
+__device__ __forceinline__ uint32_t core_offset(int r, int m, int KS) {
+  return (uint32_t)((r >> 3) * (KS / 8) * 128 + (m >> 3) * 128 + (r & 7) * 16 + (m & 7) * 2);
 }
 
 __device__ __forceinline__ uint64_t make_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -222,23 +232,22 @@ __device__ __forceinline__ uint64_t make_smem_desc(uint32_t saddr, uint32_t lbo,
   return d;
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128.
-__device__ __forceinline__ uint32_t make_idesc_tf32(int N) {
+// Instruction descriptor: kind::f16, D = F32, A = B = F16, both K-major, M = 128.
+__device__ __forceinline__ uint32_t make_idesc_f16(int N) {
   uint32_t d = 0;
   d |= 1u << 4;                       // D format F32
-  d |= 2u << 7;                       // A format TF32
-  d |= 2u << 10;                      // B format TF32
+  // A and B format F16 (0 in bits 7-9 and 10-12), no negation, K-major
   d |= (uint32_t)(N >> 3) << 17;      // N / 8
   d |= (uint32_t)(128 >> 4) << 24;    // M / 16
   return d;
 }
 
-__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                            uint32_t idesc, int accumulate) {
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                           uint32_t idesc, int accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       :
       : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
@@ -354,52 +363,71 @@ __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Writes rows [row0, row0+nrows) of a panel (pitch KP floats, j valid
-// columns) as TF32 hi and lo parts into 128-row core-matrix tiles; rows and
-// columns outside the valid range are zero.
-__device__ __forceinline__ void stage_split(const float* P, int KP, int row0, int nrows, int j, int K8,
-                                            unsigned char* hi, unsigned char* lo) {
-  const int chunks = kTileN * (K8 / 4);
+// columns), times the power of two sc, as FP16 hi and lo parts
+// (hi = fp16(x sc), lo = fp16(x sc - hi), both rounded to nearest) into
+// 128-row core-matrix tiles of KS columns; rows and columns outside the valid
+// range are zero.
+__device__ __forceinline__ void stage_split(const float* P, int KP, int row0, int nrows, int j, int KS,
+                                            float sc, unsigned char* hi, unsigned char* lo) {
+  const int chunks = kTileN * (KS / 8);
   for (int c = threadIdx.x; c < chunks; c += kDelNT) {
-    // c = ((row group * K8/4) + k chunk) * 8 + row within group: eight lanes
+    // c = ((row group * KS/8) + k chunk) * 8 + row within group: eight lanes
     // write one 128-byte core matrix, conflict-free
     const int r8 = c & 7, rest = c >> 3;
-    const int kc = rest % (K8 / 4), grp = rest / (K8 / 4);
-    const int r = grp * 8 + r8, m0 = kc * 4;
+    const int kc = rest % (KS / 8), grp = rest / (KS / 8);
+    const int r = grp * 8 + r8, m0 = kc * 8;
+    // two 16-byte loads per chunk (rows are 16-byte aligned: KP % 4 == 0);
+    // the second only below j <= KP - 4, so never past the row
+    float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+    if (r < nrows && m0 < j) xa = *reinterpret_cast<const float4*>(P + (row0 + r) * KP + m0);
+    if (r < nrows && m0 + 4 < j) xb = *reinterpret_cast<const float4*>(P + (row0 + r) * KP + m0 + 4);
+    const float xs[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
     uint32_t h[4], l[4];
-    // one 16-byte load per chunk (rows are 16-byte aligned: KP % 4 == 0)
-    float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r < nrows && m0 < j) x4 = *reinterpret_cast<const float4*>(P + (row0 + r) * KP + m0);
-    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float x = (m0 + q < j) ? xs[q] : 0.f;
-      h[q] = f32_to_tf32_rna(x);
-      l[q] = f32_to_tf32_rna(x - __uint_as_float(h[q]));
+      uint32_t hh[2], ll[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float x = (m0 + 2 * q + e < j) ? xs[2 * q + e] * sc : 0.f;
+        hh[e] = f32_to_f16_bits(x);
+        ll[e] = f32_to_f16_bits(x - f16_bits_to_f32(hh[e]));
+      }
+      h[q] = hh[0] | (hh[1] << 16);
+      l[q] = ll[0] | (ll[1] << 16);
     }
-    const uint32_t off = core_offset(r, m0, K8);
+    const uint32_t off = core_offset(r, m0, KS);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
-// Thread 0: issues the 3-pass split-TF32 product of one 128 x N16 tile over
-// K8 into the TMEM accumulator at column col (the caller has fenced and
+// Power of two that brings a panel's largest magnitude mx into [2^14, 2^15)
+// (1 for an all-zero panel), so that hi stays below FP16's largest value.
+__device__ __forceinline__ float stage_scale(float mx) {
+  if (!(mx > 0.f)) return 1.f;
+  int e;
+  (void)frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, 15 - e);
+}
+
+// Thread 0: issues the 3-pass split-FP16 product of one 128 x N16 tile over
+// KS into the TMEM accumulator at column col (the caller has fenced and
 // synchronised the staged operands).
 __device__ __forceinline__ void tc_issue_product(const TcState* tc, uint32_t col, const unsigned char* Ahi,
                                                  const unsigned char* Alo, const unsigned char* Bhi,
-                                                 const unsigned char* Blo, int K8, int N16) {
-  const uint32_t sbo = (uint32_t)(K8 / 4) * 128u, lbo = 128u;
-  const uint32_t idesc = make_idesc_tf32(N16);
+                                                 const unsigned char* Blo, int KS, int N16) {
+  const uint32_t sbo = (uint32_t)(KS / 8) * 128u, lbo = 128u;
+  const uint32_t idesc = make_idesc_f16(N16);
   const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
   const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
   const uint32_t d = tc->tmem + col;
   int acc = 0;
-  for (int kb = 0; kb < K8 / 8; ++kb) {
-    const uint32_t koff = (uint32_t)kb * 256u;
-    tc_mma_tf32(d, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo), idesc, acc);
+  for (int kb = 0; kb < KS / 16; ++kb) {
+    const uint32_t koff = (uint32_t)kb * 256u;  // two core matrices of 8 FP16 along K
+    tc_mma_f16(d, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo), idesc, acc);
     acc = 1;
-    tc_mma_tf32(d, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_lo + koff, lbo, sbo), idesc, 1);
-    tc_mma_tf32(d, make_smem_desc(a_lo + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo), idesc, 1);
+    tc_mma_f16(d, make_smem_desc(a_hi + koff, lbo, sbo), make_smem_desc(b_lo + koff, lbo, sbo), idesc, 1);
+    tc_mma_f16(d, make_smem_desc(a_lo + koff, lbo, sbo), make_smem_desc(b_hi + koff, lbo, sbo), idesc, 1);
   }
 }
 
@@ -431,10 +459,10 @@ __device__ inline bool tc_commit_wait(TcState* tc) {
 template <bool kTR>
 __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                             const float* Pw, int KP, int L, int j, unsigned char* stage,
-                                            const DelLayout& lay, int* status, float* dtile,
-                                            const void* tmap, int chain) {
-  const int K8 = (j + 7) / 8 * 8;
-  const size_t tile_bytes = (size_t)kTileN * lay.K8 * 4;
+                                            const DelLayout& lay, int* status, uint32_t* wred,
+                                            float* dtile, const void* tmap, int chain) {
+  const int KS = (j + 15) / 16 * 16;
+  const size_t tile_bytes = (size_t)kTileN * lay.KS * 2;
   const int LB = (L + kTileN - 1) / kTileN;  // blocks of 128 rows / columns
   const int UB = lay.ub;                     // U blocks staged together
   unsigned char* Whi = stage;
@@ -445,19 +473,55 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   const int quarter = warp & 3, half = warp >> 2;
   const int m = 32 * quarter + lane;               // G column nb + m of a tile
   int nhalf = 0;                                   // half tiles handed to the TMA unit
+  // per panel (U up, W up, U down, W down) the scale 2^a that brings its
+  // largest magnitude over the j valid columns (zeros beyond) into
+  // [2^14, 2^15): a = 141 - E for the largest biased exponent E, the four
+  // exponent bytes of a warp packed into one word of wred
+  int ea[4];
+  {
+    const int j4 = (j + 3) >> 2;
+    uint32_t ex[4] = {0u, 0u, 0u, 0u};
+    for (int e = threadIdx.x; e < L * j4; e += kDelNT) {
+      const int r = e / j4, c4 = e - r * j4;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float* P = ((a & 1) ? Pw : Pu) + (size_t)(a >> 1) * del_spin_stride(L, KP);
+        const uint4 x = *reinterpret_cast<const uint4*>(P + r * KP + 4 * c4);
+        const uint32_t mx = max(max(x.x & 0x7fffffffu, x.y & 0x7fffffffu),
+                                max(x.z & 0x7fffffffu, x.w & 0x7fffffffu));
+        ex[a] = max(ex[a], mx >> 23);
+      }
+    }
+    uint32_t packed = 0u;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) packed |= __reduce_max_sync(0xffffffffu, ex[a]) << (8 * a);
+    if (lane == 0) wred[warp] = packed;
+    __syncthreads();
+    uint32_t E[4] = {0u, 0u, 0u, 0u};
+    for (int w = 0; w < kDelNT / 32; ++w) {
+      const uint32_t v = wred[w];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) E[a] = max(E[a], (v >> (8 * a)) & 255u);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ea[a] = E[a] == 0u ? 0 : min(141 - (int)E[a], 127);
+  }
   for (int sp = 0; sp < 2; ++sp) {
     float* G = sp ? Gd : Gu;
     const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
     const float* W = Pw + (size_t)sp * del_spin_stride(L, KP);
+    const float su = ldexpf(1.f, sp ? ea[2] : ea[0]), sw = ldexpf(1.f, sp ? ea[3] : ea[1]);
+    // the product comes back scaled by su sw: undone exactly in the epilogue
+    const float ds = ldexpf(1.f, -(sp ? ea[2] + ea[3] : ea[0] + ea[1]));
     for (int nbi = 0; nbi < LB; ++nbi) {  // block of G columns = rows of W
       const int nb = nbi * kTileN, nN = min(kTileN, L - nb);
-      stage_split(W, KP, nb, nN, j, K8, Whi, Wlo);
+      stage_split(W, KP, nb, nN, j, KS, sw, Whi, Wlo);
       for (int mg = 0; mg < LB; mg += UB) {  // group of U blocks = blocks of G rows
         const int ub = min(UB, LB - mg);
         if (!(UB == LB && nbi > 0)) {  // all of U staged once per spin when it fits
           for (int u = 0; u < ub; ++u) {
             const int mb = (mg + u) * kTileN;
-            stage_split(U, KP, mb, min(kTileN, L - mb), j, K8, stage + (2 + 2 * u) * tile_bytes,
+            stage_split(U, KP, mb, min(kTileN, L - mb), j, KS, su, stage + (2 + 2 * u) * tile_bytes,
                         stage + (3 + 2 * u) * tile_bytes);
           }
         }
@@ -469,7 +533,7 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
           for (int u = 0; u < ub; ++u) {
             const int nM = min(kTileN, L - (mg + u) * kTileN);
             tc_issue_product(tc, (uint32_t)(u * kTileN), Whi, Wlo, stage + (2 + 2 * u) * tile_bytes,
-                             stage + (3 + 2 * u) * tile_bytes, K8, (nM + 15) / 16 * 16);
+                             stage + (3 + 2 * u) * tile_bytes, KS, (nM + 15) / 16 * 16);
           }
         }
         if (!tc_commit_wait(tc)) {
@@ -504,7 +568,7 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
                   // rows >= nM and columns >= nN lie outside G and are clipped
                   float* dt = dbuf + (cb - r0) * kTileN + m;
 #pragma unroll
-                  for (int q = 0; q < 16; ++q) dt[q * kTileN] = v[q];
+                  for (int q = 0; q < 16; ++q) dt[q * kTileN] = v[q] * ds;
                 }
               }
               tc_fence_before();
@@ -526,7 +590,7 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
                   float* g = G + (size_t)(mb + cb) * ld + nb + m;
 #pragma unroll
                   for (int q = 0; q < 16; ++q)
-                    if (cb + q < nM) g[(size_t)q * ld] += v[q];
+                    if (cb + q < nM) g[(size_t)q * ld] += v[q] * ds;
                 }
               }
             }
@@ -549,16 +613,16 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
 
 __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                      const float* Pw, int KP, int L, int j, unsigned char* stage,
-                                     const DelLayout& lay, int* status, float* dtile = nullptr,
-                                     const void* tmap = nullptr, int chain = 0) {
+                                     const DelLayout& lay, int* status, uint32_t* wred,
+                                     float* dtile = nullptr, const void* tmap = nullptr, int chain = 0) {
   if (tc->failed) {
     flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
     return;
   }
   if (dtile)
-    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, dtile, tmap, chain);
+    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, dtile, tmap, chain);
   else
-    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, nullptr, nullptr, 0);
+    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, nullptr, nullptr, 0);
 }
 
 // One pass of both spins with RB rows per warp in flight and CPL columns per

@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     auto flush = [&]() {
       if (j == 0) return;
       if (use_tc)
-        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status, dtile, gc.tmapG,
-                      ip.chain);
+        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status,
+                      reinterpret_cast<uint32_t*>(red), dtile, gc.tmapG, ip.chain);
       else
         flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
       __syncthreads();
