@@ -59,12 +59,12 @@ enum {
     HFQMC_F64_RANK1 = 0,   /* FP64 G, rank-1 update per accepted flip (baseline) */
     HFQMC_F32_RANK1 = 1,   /* FP32 G, rank-1 update per accepted flip            */
     HFQMC_F32_DELAYED = 2  /* FP32 G, k accepted flips gathered into one rank-k
-                              update (split-TF32 tensor-core GEMM)                */
+                              update (split-FP16 tensor-core GEMM)                */
 };
 enum { HFQMC_METROPOLIS = 0, HFQMC_HEAT_BATH = 1 };
 enum {
     HFQMC_FLUSH_AUTO = 0,    /* tensor cores where available                    */
-    HFQMC_FLUSH_TCGEN05 = 1, /* rank-k flush on tcgen05 (kind::tf32, 3 passes)  */
+    HFQMC_FLUSH_TCGEN05 = 1, /* rank-k flush on tcgen05 (kind::f16, 3 passes)   */
     HFQMC_FLUSH_FFMA = 2     /* rank-k flush on FP32 FMA (CUDA cores)           */
 };
 

@@ -9,7 +9,7 @@
 // whose entries cost O(j) each (the base column / row entry plus a length-j
 // dot product with the panels).  Every k accepted flips the panels are
 // flushed, G += U W^T -- a dense L x L x k contraction per spin (tcgen05
-// tensor cores with split TF32, or FP32 FMA).  In exact arithmetic this is
+// tensor cores with scaled split FP16, or FP32 FMA).  In exact arithmetic this is
 // the Hirsch-Fye rank-1 update applied k times; only the rounding differs.
 // The panels are also flushed before every measurement and every FP64
 // recompute (every n_wrap accepted flips).
