@@ -45,7 +45,7 @@ struct TuneEntry {
   int L_max, k, n_wrap;
 };
 const TuneEntry kTuneTable[] = {
-    {64, 8, 8192},    {128, 24, 8192},   {144, 16, 16384},
+    {64, 32, 8192},   {128, 32, 8192},   {144, 32, 16384},
     {176, 24, 16384}, {1024, 16, 16384},
 };
 
