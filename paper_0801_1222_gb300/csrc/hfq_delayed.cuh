@@ -202,15 +202,21 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// FP32 -> FP16 (round to nearest even) as the 16-bit pattern, and back
-__device__ __forceinline__ uint32_t f32_to_f16_bits(float x) {
-  unsigned short h;
-  asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+// Two FP32 values -> FP16 (round to nearest even) packed, x0 in the low half
+// (the lower address), and the two halves back to FP32
+__device__ __forceinline__ uint32_t f32x2_to_f16x2(float x0, float x1) {
+  uint32_t h;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
   return h;
 }
-__device__ __forceinline__ float f16_bits_to_f32(uint32_t h) {
+__device__ __forceinline__ float f16_lo_to_f32(uint32_t h) {
   float x;
-  asm("cvt.f32.f16 %0, %1;" : "=f"(x) : "h"((unsigned short)h));
+  asm("cvt.f32.f16 %0, %1;" : "=f"(x) : "h"((unsigned short)(h & 0xffffu)));
+  return x;
+}
+__device__ __forceinline__ float f16_hi_to_f32(uint32_t h) {
+  float x;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(x) : "h"((unsigned short)(h >> 16)));
   return x;
 }
 
@@ -385,15 +391,10 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      uint32_t hh[2], ll[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float x = (m0 + 2 * q + e < j) ? xs[2 * q + e] * sc : 0.f;
-        hh[e] = f32_to_f16_bits(x);
-        ll[e] = f32_to_f16_bits(x - f16_bits_to_f32(hh[e]));
-      }
-      h[q] = hh[0] | (hh[1] << 16);
-      l[q] = ll[0] | (ll[1] << 16);
+      const float x0 = (m0 + 2 * q < j) ? xs[2 * q] * sc : 0.f;
+      const float x1 = (m0 + 2 * q + 1 < j) ? xs[2 * q + 1] * sc : 0.f;
+      h[q] = f32x2_to_f16x2(x0, x1);
+      l[q] = f32x2_to_f16x2(x0 - f16_lo_to_f32(h[q]), x1 - f16_hi_to_f32(h[q]));
     }
     const uint32_t off = core_offset(r, m0, KS);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -408,6 +409,50 @@ __device__ __forceinline__ float stage_scale(float mx) {
   int e;
   (void)frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
   return ldexpf(1.f, 15 - e);
+}
+
+// Per panel (U up, W up, U down, W down) the exponent a of the scale 2^a
+// that brings its largest magnitude over the j valid columns (zeros beyond)
+// into [2^14, 2^15): a = 141 - E for the largest biased exponent E (0 for an
+// all-zero panel).  A thread takes whole rows; the four exponent bytes of a
+// warp travel packed in one word of wred (kDelNT / 32 words, one barrier).
+__device__ __forceinline__ void panel_scales(const float* Pu, const float* Pw, int KP, int L, int j,
+                                             uint32_t* wred, int* ea) {
+  const int j4 = (j + 3) >> 2;
+  const int stride = del_spin_stride(L, KP);
+  uint32_t ex[4] = {0u, 0u, 0u, 0u};
+  for (int r = threadIdx.x; r < 2 * L; r += kDelNT) {
+    const int sp = r >= L, row = r - sp * L;
+    const uint4* U = reinterpret_cast<const uint4*>(Pu + (size_t)sp * stride + row * KP);
+    const uint4* W = reinterpret_cast<const uint4*>(Pw + (size_t)sp * stride + row * KP);
+    uint32_t eu = 0u, ew = 0u;
+    for (int c = 0; c < j4; ++c) {
+      const uint4 x = U[c], y = W[c];
+      eu = max(eu, max(max(x.x & 0x7fffffffu, x.y & 0x7fffffffu), max(x.z & 0x7fffffffu, x.w & 0x7fffffffu)));
+      ew = max(ew, max(max(y.x & 0x7fffffffu, y.y & 0x7fffffffu), max(y.z & 0x7fffffffu, y.w & 0x7fffffffu)));
+    }
+    if (sp) {
+      ex[2] = max(ex[2], eu >> 23);
+      ex[3] = max(ex[3], ew >> 23);
+    } else {
+      ex[0] = max(ex[0], eu >> 23);
+      ex[1] = max(ex[1], ew >> 23);
+    }
+  }
+  uint32_t packed = 0u;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) packed |= __reduce_max_sync(0xffffffffu, ex[a]) << (8 * a);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = packed;
+  __syncthreads();
+  uint32_t E[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int w = 0; w < kDelNT / 32; ++w) {
+    const uint32_t v = wred[w];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) E[a] = max(E[a], (v >> (8 * a)) & 255u);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) ea[a] = E[a] == 0u ? 0 : min(141 - (int)E[a], 127);
 }
 
 // Thread 0: issues the 3-pass split-FP16 product of one 128 x N16 tile over
@@ -473,39 +518,8 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   const int quarter = warp & 3, half = warp >> 2;
   const int m = 32 * quarter + lane;               // G column nb + m of a tile
   int nhalf = 0;                                   // half tiles handed to the TMA unit
-  // per panel (U up, W up, U down, W down) the scale 2^a that brings its
-  // largest magnitude over the j valid columns (zeros beyond) into
-  // [2^14, 2^15): a = 141 - E for the largest biased exponent E, the four
-  // exponent bytes of a warp packed into one word of wred
   int ea[4];
-  {
-    const int j4 = (j + 3) >> 2;
-    uint32_t ex[4] = {0u, 0u, 0u, 0u};
-    for (int e = threadIdx.x; e < L * j4; e += kDelNT) {
-      const int r = e / j4, c4 = e - r * j4;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float* P = ((a & 1) ? Pw : Pu) + (size_t)(a >> 1) * del_spin_stride(L, KP);
-        const uint4 x = *reinterpret_cast<const uint4*>(P + r * KP + 4 * c4);
-        const uint32_t mx = max(max(x.x & 0x7fffffffu, x.y & 0x7fffffffu),
-                                max(x.z & 0x7fffffffu, x.w & 0x7fffffffu));
-        ex[a] = max(ex[a], mx >> 23);
-      }
-    }
-    uint32_t packed = 0u;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) packed |= __reduce_max_sync(0xffffffffu, ex[a]) << (8 * a);
-    if (lane == 0) wred[warp] = packed;
-    __syncthreads();
-    uint32_t E[4] = {0u, 0u, 0u, 0u};
-    for (int w = 0; w < kDelNT / 32; ++w) {
-      const uint32_t v = wred[w];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) E[a] = max(E[a], (v >> (8 * a)) & 255u);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) ea[a] = E[a] == 0u ? 0 : min(141 - (int)E[a], 127);
-  }
+  panel_scales(Pu, Pw, KP, L, j, wred, ea);
   for (int sp = 0; sp < 2; ++sp) {
     float* G = sp ? Gd : Gu;
     const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
