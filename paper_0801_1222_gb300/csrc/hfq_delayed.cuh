@@ -368,18 +368,30 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Writes rows [row0, row0+nrows) of a panel (pitch KP floats, j valid
-// columns), times the power of two sc, as FP16 hi and lo parts
-// (hi = fp16(x sc), lo = fp16(x sc - hi), both rounded to nearest) into
-// 128-row core-matrix tiles of KS columns; rows and columns outside the valid
-// range are zero.
-__device__ __forceinline__ void stage_split(const float* P, int KP, int row0, int nrows, int j, int KS,
-                                            float sc, unsigned char* hi, unsigned char* lo) {
-  const int chunks = kTileN * (KS / 8);
-  for (int c = threadIdx.x; c < chunks; c += kDelNT) {
-    // c = ((row group * KS/8) + k chunk) * 8 + row within group: eight lanes
+// Writes the tiles of one flush group in one pass: W block rows
+// [nb, nb + nN) when doW (to W hi / lo at stage, stage + tile_bytes) and U
+// blocks mg .. mg + ub - 1 when doU (to stage + (2 + 2u) tile_bytes), each
+// row of a panel (pitch KP floats, j valid columns) times the power of two
+// sw or su, as FP16 hi and lo parts (hi = fp16(x s), lo = fp16(x s - hi),
+// both rounded to nearest) in 128-row core-matrix tiles of KS columns; rows
+// and columns outside the valid range are zero.
+__device__ __forceinline__ void stage_group(const float* W, int nb, int nN, bool doW, const float* U, int mg,
+                                            int ub, bool doU, int L, int KP, int j, int KS, float sw, float su,
+                                            unsigned char* stage, size_t tile_bytes) {
+  const int cpt = kTileN * (KS / 8);  // 16-byte chunks per tile
+  const int nt = (doW ? 1 : 0) + (doU ? ub : 0);
+  for (int c = threadIdx.x; c < nt * cpt; c += kDelNT) {
+    const int t = c / cpt, cc = c - t * cpt;
+    const bool isW = doW && t == 0;
+    const int u = t - (doW ? 1 : 0);
+    const float* P = isW ? W : U;
+    const int row0 = isW ? nb : (mg + u) * kTileN;
+    const int nrows = isW ? nN : min(kTileN, L - row0);
+    const float sc = isW ? sw : su;
+    unsigned char* hi = isW ? stage : stage + (size_t)(2 + 2 * u) * tile_bytes;
+    // cc = ((row group * KS/8) + k chunk) * 8 + row within group: eight lanes
     // write one 128-byte core matrix, conflict-free
-    const int r8 = c & 7, rest = c >> 3;
+    const int r8 = cc & 7, rest = cc >> 3;
     const int kc = rest % (KS / 8), grp = rest / (KS / 8);
     const int r = grp * 8 + r8, m0 = kc * 8;
     // two 16-byte loads per chunk (rows are 16-byte aligned: KP % 4 == 0);
@@ -398,17 +410,8 @@ __device__ __forceinline__ void stage_split(const float* P, int KP, int row0, in
     }
     const uint32_t off = core_offset(r, m0, KS);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<uint4*>(hi + tile_bytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
   }
-}
-
-// Power of two that brings a panel's largest magnitude mx into [2^14, 2^15)
-// (1 for an all-zero panel), so that hi stays below FP16's largest value.
-__device__ __forceinline__ float stage_scale(float mx) {
-  if (!(mx > 0.f)) return 1.f;
-  int e;
-  (void)frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-  return ldexpf(1.f, 15 - e);
 }
 
 // Per panel (U up, W up, U down, W down) the exponent a of the scale 2^a
@@ -529,16 +532,11 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
     const float ds = ldexpf(1.f, -(sp ? ea[2] + ea[3] : ea[0] + ea[1]));
     for (int nbi = 0; nbi < LB; ++nbi) {  // block of G columns = rows of W
       const int nb = nbi * kTileN, nN = min(kTileN, L - nb);
-      stage_split(W, KP, nb, nN, j, KS, sw, Whi, Wlo);
       for (int mg = 0; mg < LB; mg += UB) {  // group of U blocks = blocks of G rows
         const int ub = min(UB, LB - mg);
-        if (!(UB == LB && nbi > 0)) {  // all of U staged once per spin when it fits
-          for (int u = 0; u < ub; ++u) {
-            const int mb = (mg + u) * kTileN;
-            stage_split(U, KP, mb, min(kTileN, L - mb), j, KS, su, stage + (2 + 2 * u) * tile_bytes,
-                        stage + (3 + 2 * u) * tile_bytes);
-          }
-        }
+        // W's block once per block, all of U once per spin when it fits
+        stage_group(W, nb, nN, mg == 0, U, mg, ub, !(UB == LB && nbi > 0), L, KP, j, KS, sw, su, stage,
+                    tile_bytes);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
