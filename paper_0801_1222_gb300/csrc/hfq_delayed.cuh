@@ -417,45 +417,24 @@ __device__ __forceinline__ void stage_group(const float* W, int nb, int nN, bool
 // Per panel (U up, W up, U down, W down) the exponent a of the scale 2^a
 // that brings its largest magnitude over the j valid columns (zeros beyond)
 // into [2^14, 2^15): a = 141 - E for the largest biased exponent E (0 for an
-// all-zero panel).  A thread takes whole rows; the four exponent bytes of a
-// warp travel packed in one word of wred (kDelNT / 32 words, one barrier).
-__device__ __forceinline__ void panel_scales(const float* Pu, const float* Pw, int KP, int L, int j,
-                                             uint32_t* wred, int* ea) {
-  const int j4 = (j + 3) >> 2;
-  const int stride = del_spin_stride(L, KP);
-  uint32_t ex[4] = {0u, 0u, 0u, 0u};
-  for (int r = threadIdx.x; r < 2 * L; r += kDelNT) {
-    const int sp = r >= L, row = r - sp * L;
-    const uint4* U = reinterpret_cast<const uint4*>(Pu + (size_t)sp * stride + row * KP);
-    const uint4* W = reinterpret_cast<const uint4*>(Pw + (size_t)sp * stride + row * KP);
-    uint32_t eu = 0u, ew = 0u;
-    for (int c = 0; c < j4; ++c) {
-      const uint4 x = U[c], y = W[c];
-      eu = max(eu, max(max(x.x & 0x7fffffffu, x.y & 0x7fffffffu), max(x.z & 0x7fffffffu, x.w & 0x7fffffffu)));
-      ew = max(ew, max(max(y.x & 0x7fffffffu, y.y & 0x7fffffffu), max(y.z & 0x7fffffffu, y.w & 0x7fffffffu)));
-    }
-    if (sp) {
-      ex[2] = max(ex[2], eu >> 23);
-      ex[3] = max(ex[3], ew >> 23);
-    } else {
-      ex[0] = max(ex[0], eu >> 23);
-      ex[1] = max(ex[1], ew >> 23);
-    }
-  }
-  uint32_t packed = 0u;
+// all-zero panel), from the byte-wise maxima each thread kept while
+// appending: exq holds the biased exponents of its largest |u| (byte 0) and
+// |w| (byte 1) for its spin sp (thread parity).  The four bytes of a warp
+// travel in one word of wred (kDelNT / 32 words, one barrier).
+__device__ __forceinline__ void panel_scales(uint32_t exq, uint32_t* wred, int* ea) {
+  uint32_t v = (threadIdx.x & 1) ? (exq << 16) : exq;  // bytes: U up, W up, U down, W down
 #pragma unroll
-  for (int a = 0; a < 4; ++a) packed |= __reduce_max_sync(0xffffffffu, ex[a]) << (8 * a);
-  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = packed;
+  for (int o = 16; o; o >>= 1) v = __vmaxu4(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
   __syncthreads();
-  uint32_t E[4] = {0u, 0u, 0u, 0u};
+  uint32_t E = 0u;
 #pragma unroll
-  for (int w = 0; w < kDelNT / 32; ++w) {
-    const uint32_t v = wred[w];
+  for (int w = 0; w < kDelNT / 32; ++w) E = __vmaxu4(E, wred[w]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) E[a] = max(E[a], (v >> (8 * a)) & 255u);
+  for (int a = 0; a < 4; ++a) {
+    const uint32_t e = (E >> (8 * a)) & 255u;
+    ea[a] = e == 0u ? 0 : min(141 - (int)e, 127);
   }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) ea[a] = E[a] == 0u ? 0 : min(141 - (int)E[a], 127);
 }
 
 // Thread 0: issues the 3-pass split-FP16 product of one 128 x N16 tile over
@@ -508,7 +487,7 @@ template <bool kTR>
 __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                             const float* Pw, int KP, int L, int j, unsigned char* stage,
                                             const DelLayout& lay, int* status, uint32_t* wred,
-                                            float* dtile, const void* tmap, int chain) {
+                                            uint32_t exq, float* dtile, const void* tmap, int chain) {
   const int KS = (j + 15) / 16 * 16;
   const size_t tile_bytes = (size_t)kTileN * lay.KS * 2;
   const int LB = (L + kTileN - 1) / kTileN;  // blocks of 128 rows / columns
@@ -522,7 +501,7 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   const int m = 32 * quarter + lane;               // G column nb + m of a tile
   int nhalf = 0;                                   // half tiles handed to the TMA unit
   int ea[4];
-  panel_scales(Pu, Pw, KP, L, j, wred, ea);
+  panel_scales(exq, wred, ea);
   for (int sp = 0; sp < 2; ++sp) {
     float* G = sp ? Gd : Gu;
     const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
@@ -625,16 +604,16 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
 
 __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                      const float* Pw, int KP, int L, int j, unsigned char* stage,
-                                     const DelLayout& lay, int* status, uint32_t* wred,
+                                     const DelLayout& lay, int* status, uint32_t* wred, uint32_t exq,
                                      float* dtile = nullptr, const void* tmap = nullptr, int chain = 0) {
   if (tc->failed) {
     flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
     return;
   }
   if (dtile)
-    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, dtile, tmap, chain);
+    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, exq, dtile, tmap, chain);
   else
-    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, nullptr, nullptr, 0);
+    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, exq, nullptr, nullptr, 0);
 }
 
 // One pass of both spins with RB rows per warp in flight and CPL columns per

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     double drift = c0.drift;
     const long long n_sweeps = a.n_warm + a.n_meas;
     int j = 0;     // pending flips in the panels
+    uint32_t exq = 0u;  // biased exponents of this thread's largest appended |u| (byte 0), |w| (byte 1)
     int par = 0;   // s_next buffer of the current round
     __syncthreads();
 
@@ -153,12 +154,13 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       if (j == 0) return;
       if (use_tc)
         flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status,
-                      reinterpret_cast<uint32_t*>(red), dtile, gc.tmapG, ip.chain);
+                      reinterpret_cast<uint32_t*>(red), exq, dtile, gc.tmapG, ip.chain);
       else
         flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
       __syncthreads();
       load_diag();
       j = 0;
+      exq = 0u;
       // the panels restart from zeros, so the dot products may run over whole
       // 16-byte chunks past column j
       zero_panels();
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           }
           const float uu = gil + ((c4[0] + c4[1]) + (c4[2] + c4[3])) - ((i == l) ? 1.f : 0.f);
           const float ww = (gli + ((r4[0] + r4[1]) + (r4[2] + r4[3]))) * f;
+          exq = __vmaxu4(exq, ((__float_as_uint(uu) << 1) >> 24) | (((__float_as_uint(ww) << 1) >> 24) << 8));
           Us[oi + j] = uu;
           Ws[oi + j] = ww;
           dg[qq] = __fmaf_rn(uu, ww, dg[qq]);
