@@ -359,18 +359,22 @@ __device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, doubl
     __syncthreads();
     for (int t = 0; t < bb; ++t) {
       const int k = k0 + t;
-      double best = -1.0;
+      // the largest |pivot| (then the lowest row) among the unused rows,
+      // compared as the magnitudes' bit patterns: for non-negative doubles
+      // their order is that of unsigned integers, and the integer compares
+      // keep the search off this part's slow FP64 pipe
+      unsigned long long best = 0ull;
       int bi = L;
       for (int i = tid; i < L; i += NT)
         if (pos[i] < 0) {
-          const double v = fabs(pan[i * PP + t]);
+          const unsigned long long v = __double_as_longlong(pan[i * PP + t]) & 0x7fffffffffffffffull;
           if (v > best) {
             best = v;
             bi = i;
           }
         }
       for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) {
           best = ov;
@@ -378,26 +382,26 @@ __device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, doubl
         }
       }
       if (lane == 0) {
-        red[warp] = best;
+        reinterpret_cast<unsigned long long*>(red)[warp] = best;
         redi[warp] = bi;
       }
       __syncthreads();
       if (warp == 0) {
-        // the warps' candidates (largest |pivot|, then lowest row), the
-        // reciprocal, and the pivot row scaled (its column-t entry becomes
-        // the reciprocal) into the slab's first KB words, which the update
-        // overwrites later; the panel's copy is replaced after the barrier
-        best = lane < NW ? red[lane] : -1.0;
+        // the warps' candidates, the reciprocal, and the pivot row scaled
+        // (its column-t entry becomes the reciprocal) into the slab's first
+        // KB words, which the update overwrites later; the panel's copy is
+        // replaced after the barrier
+        best = lane < NW ? reinterpret_cast<const unsigned long long*>(red)[lane] : 0ull;
         bi = lane < NW ? redi[lane] : L;
         for (int o = 16; o; o >>= 1) {
-          const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ov > best || (ov == best && oi < bi)) {
             best = ov;
             bi = oi;
           }
         }
-        const bool ok = best > 0.0 && bi < L;
+        const bool ok = best > 0ull && bi < L;
         const double inv = ok ? 1.0 / pan[bi * PP + t] : 0.0;
         if (ok && lane < bb) slab[lane] = (lane == t) ? inv : pan[bi * PP + lane] * inv;
         if (lane == 0) {
