@@ -357,22 +357,13 @@ __device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, doubl
     for (int i = warp; i < L; i += NW)
       if (lane < bb) pan[i * PP + lane] = B[(size_t)i * L + k0 + lane];
     __syncthreads();
-    for (int t = 0; t < bb; ++t) {
-      const int k = k0 + t;
-      // the largest |pivot| (then the lowest row) among the unused rows,
-      // compared as the magnitudes' bit patterns: for non-negative doubles
-      // their order is that of unsigned integers, and the integer compares
-      // keep the search off this part's slow FP64 pipe
-      unsigned long long best = 0ull;
-      int bi = L;
-      for (int i = tid; i < L; i += NT)
-        if (pos[i] < 0) {
-          const unsigned long long v = __double_as_longlong(pan[i * PP + t]) & 0x7fffffffffffffffull;
-          if (v > best) {
-            best = v;
-            bi = i;
-          }
-        }
+    // the largest |pivot| (then the lowest row) among the unused rows,
+    // compared as the magnitudes' bit patterns: for non-negative doubles
+    // their order is that of unsigned integers, and the integer compares
+    // keep the search off this part's slow FP64 pipe.  Each warp's best
+    // candidate goes to red / redi: for the panel's first column from a
+    // search here, for every later column from the rows just updated.
+    auto offer = [&](unsigned long long best, int bi) {
       for (int o = 16; o; o >>= 1) {
         const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -385,14 +376,30 @@ __device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, doubl
         reinterpret_cast<unsigned long long*>(red)[warp] = best;
         redi[warp] = bi;
       }
-      __syncthreads();
+    };
+    {
+      unsigned long long best = 0ull;
+      int bi = L;
+      for (int i = tid; i < L; i += NT)
+        if (pos[i] < 0) {
+          const unsigned long long v = __double_as_longlong(pan[i * PP]) & 0x7fffffffffffffffull;
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
+      offer(best, bi);
+    }
+    __syncthreads();
+    for (int t = 0; t < bb; ++t) {
+      const int k = k0 + t;
       if (warp == 0) {
         // the warps' candidates, the reciprocal, and the pivot row scaled
         // (its column-t entry becomes the reciprocal) into the slab's first
         // KB words, which the update overwrites later; the panel's copy is
         // replaced after the barrier
-        best = lane < NW ? reinterpret_cast<const unsigned long long*>(red)[lane] : 0ull;
-        bi = lane < NW ? redi[lane] : L;
+        unsigned long long best = lane < NW ? reinterpret_cast<const unsigned long long*>(red)[lane] : 0ull;
+        int bi = lane < NW ? redi[lane] : L;
         for (int o = 16; o; o >>= 1) {
           const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -413,10 +420,14 @@ __device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, doubl
           }
         }
       }
+      // warp 0 has read every candidate before this barrier, so the
+      // candidates of column t + 1 may overwrite them after it
       __syncthreads();
       const int p = *s_piv;
       if (p < 0) return -1;
       const double inv = *s_inv;
+      unsigned long long best = 0ull;
+      int bi = L;
       for (int i = tid; i < L; i += NT) {
         double* pr = pan + i * PP;
         if (i == p) {
@@ -430,7 +441,15 @@ __device__ int gj_invert_blocked(double* B, int L, double* red, int* redi, doubl
         for (int u = 0; u < KB; ++u)
           if (u < bb && u != t) pr[u] = fma(-c, slab[u], pr[u]);
         pr[t] = -c * inv;
+        if (t + 1 < bb && pos[i] < 0) {
+          const unsigned long long v = __double_as_longlong(pr[t + 1]) & 0x7fffffffffffffffull;
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
       }
+      if (t + 1 < bb) offer(best, bi);
       __syncthreads();
     }
     // the pivot rows of the other columns, then their rank-b update, in
