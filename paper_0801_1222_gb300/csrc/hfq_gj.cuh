@@ -5,19 +5,20 @@
 // followed by the drift check max |G_fast - G_fresh|.
 //
 // Two algorithms, both Gauss-Jordan elimination with partial pivoting by one
-// CTA, with per pivot column three barriers (pivot search, row swap + scale,
-// elimination), bound by the FP64 pipe (about 2 DFMA/clk/SM on GB300):
+// CTA, bound by the FP64 pipe (about 2 DFMA/clk/SM on GB300):
 //  * recompute_green: on the augmented L x 2L matrix [A | M], 1.5 L^3 DFMA
 //    per spin.  Used by the entry point that allocates nothing.
 //  * recompute_green_inv: G = B^{-1} with B = M^{-1}(1 + D) - D inverted in
 //    place, L^3 DFMA per spin on an L x L workspace.  Used by every sweep
 //    kernel and the initialisation.  Two forms of the inversion:
-//    gj_invert_inplace (row interchanges) on a workspace in shared memory
+//    gj_invert_inplace (row interchanges; three barriers per pivot column:
+//    search, swap + scale, elimination) on a workspace in shared memory
 //    (rank-1 paths and initialisation, Lambda <= 168) or in HBM when nothing
 //    else fits; gj_invert_blocked (implicit pivoting, kGjPanel columns per
-//    panel in shared memory) on the chain's HBM workspace, which it reads and
-//    writes once per panel instead of once per pivot column -- the FP32
-//    delayed path always, the initialisation whenever the panel fits.
+//    panel in shared memory, two barriers per pivot column) on the chain's
+//    HBM workspace, which it reads and writes once per panel instead of once
+//    per pivot column -- the FP32 delayed path always, the initialisation
+//    whenever the panel fits.
 #pragma once
 #include "hfq_device.cuh"
 
