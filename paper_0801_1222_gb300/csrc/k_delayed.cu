@@ -325,9 +325,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           measure_rows(Gu, Gd, ld, L, part, gsum);
         for (int k = tid; k < L; k += NT) {
           const double gu = (double)gsum[k] / (double)L, gd = (double)gsum[L + k] / (double)L;
-          ip.acc[k] += gu;
-          ip.acc[L + k] += gd;
-          ip.bins[(size_t)b * L + k] += 0.5 * (gu + gd);
+          // the three accumulators loaded before any is stored: one L2 round trip
+          double* bk = ip.bins + (size_t)b * L;
+          const double a0 = ip.acc[k], a1 = ip.acc[L + k], b0 = bk[k];
+          ip.acc[k] = a0 + gu;
+          ip.acc[L + k] = a1 + gd;
+          bk[k] = b0 + 0.5 * (gu + gd);
         }
         float v = 0.f;
 #pragma unroll
@@ -340,8 +343,9 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         for (int e = tid; e < 2 * L; e += NT) gsum[e] = 0.f;
         v = block_sum_f(v, reinterpret_cast<float*>(red));
         if (tid == 0) {
-          ip.accD[0] += (double)v / (double)L;
-          ip.accD[1 + b] += (double)v / (double)L;
+          const double d0 = ip.accD[0], d1 = ip.accD[1 + b];
+          ip.accD[0] = d0 + (double)v / (double)L;
+          ip.accD[1 + b] = d1 + (double)v / (double)L;
         }
       }
       __syncthreads();
