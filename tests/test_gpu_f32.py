@@ -101,6 +101,29 @@ def test_delayed_U0_zero_panels_keep_G0():
         assert np.max(np.abs(G[:L] - inputs.bethe_G0_tau(10.0, L))) < 1e-6
     ctx.close()
 
+
+def test_half_filling_spin_invariant():
+    """At half filling with the particle-hole symmetric bath every field
+    configuration has G_dn = 1 - G_up^T (pinned on the oracle).  The FP64
+    rank-1 path keeps it to 1e-10; the FP32 delayed path, which updates the
+    two spins independently (separate panels, scale exponents, tensor-core
+    products and TMA reduces), to its drift level between recomputes."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    for prec, tol in (("f64_rank1", 1e-10), ("f32_delayed", 1e-3)):
+        ctx = h.HFQMC(20.0, 5.0, [0.1, 20.0 / 240], [2, 2], seed=6, precision=prec, n_wrap=64,
+                      drift_fail=1.0)
+        ctx.set_G0(0, inputs.bethe_G0_tau(20.0, 200))
+        ctx.set_G0(1, inputs.bethe_G0_tau(20.0, 240))
+        ctx.sweep(1, 2)
+        for g in range(2):
+            for c in range(2):
+                ch = ctx.get_chain(g, c)
+                assert ch["accepted"] > 0
+                L = ch["Gup"].shape[0]
+                assert np.max(np.abs(ch["Gdn"] - (np.eye(L) - ch["Gup"].T))) < tol, (prec, g, c)
+        ctx.close()
+
 def test_tcgen05_flush_matches_ffma_flush():
     from paper_0801_1222_gb300 import inputs
     h = lib()
