@@ -77,7 +77,7 @@ typedef struct {
     int n_wrap;         /* FP64 recompute every n_wrap accepted flips; 0 = per-Lambda table; <0 = never */
     int accept_rule;    /* HFQMC_METROPOLIS (accept iff u < R) | HFQMC_HEAT_BATH (u (1+R) < R) */
     double drift_warn;  /* recorded only */
-    double drift_fail;  /* hfqmc_sweep returns HFQMC_EDRIFT above this (<= 0: never) */
+    double drift_fail;  /* hfqmc_sweep returns HFQMC_EDRIFT above this (<= 0: never; default 1e-1) */
     void *cuda_stream;  /* cudaStream_t to order all work on; NULL = library-owned stream */
     int autotune;       /* 1: k / n_wrap left 0 come from the per-Lambda table (the caller's
                            tune_table if given, else the built-in one measured on GB300);
@@ -123,8 +123,11 @@ typedef struct {
 typedef struct hfqmc_ctx hfqmc_ctx;
 
 /* Fills *opts with defaults: F32_DELAYED, k = 0, n_wrap = 0 (table), Metropolis,
- * drift_warn 1e-6, drift_fail 1e-3, own stream, autotune on, flush auto,
- * graphs on, no allocator hooks. */
+ * drift_warn 1e-6, drift_fail 1e-1, own stream, autotune on, flush auto,
+ * graphs on, no allocator hooks.  drift_fail guards against a broken chain:
+ * at the table's N_wrap the FP32 matrix drift max|G_fast - G_fresh| reaches
+ * a few 1e-2 (maximum over chains) while G(tau) stays within its 1e-5
+ * criterion, so the default sits an order of magnitude above that. */
 void hfqmc_default_opts(hfqmc_opts *opts);
 
 /* Creates a context for one beta and one U over n_grids dtau grids.

@@ -242,7 +242,7 @@ class HFQMC:
     """One context: several (U, dtau) grids x chains, fixed beta."""
 
     def __init__(self, beta, U, dtau, chains_per_grid, seed=1, precision="f32_delayed", k=0,
-                 n_wrap=0, accept_rule="metropolis", drift_fail=1e-3, flush="auto",
+                 n_wrap=0, accept_rule="metropolis", drift_fail=1e-1, flush="auto",
                  use_graph=True, stream=None, torch_alloc=True, resident_kb=0, gj_smem=0,
                  gtile=0, tune=None, autotune=True):
         o = hfqmc_default_opts()

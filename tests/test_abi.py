@@ -25,7 +25,7 @@ def test_exports_every_declared_symbol(lib):
 def test_default_opts(lib):
     o = lib.hfqmc_default_opts()
     assert o.precision == lib.PRECISION["f32_delayed"]
-    assert o.accept_rule == 0 and o.use_graph == 1 and o.drift_fail == 1e-3
+    assert o.accept_rule == 0 and o.use_graph == 1 and o.drift_fail == 1e-1
 
 
 @pytest.mark.parametrize("beta,dtau,chains,what", [
