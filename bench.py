@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
-TRAFFIC_PER_1000_SWEEPS = 0.390861824e9 + 17.042746880e9  # dram read + write of one launch (ncu)
+TRAFFIC_PER_1000_SWEEPS = None  # dram read + write of one launch (ncu); unset until recaptured for the current kernel
 
 
 def parse():

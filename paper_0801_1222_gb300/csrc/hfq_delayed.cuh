@@ -663,6 +663,90 @@ __device__ __forceinline__ void measure_rows_batched(const float* __restrict__ G
   }
 }
 
+// The same sums with the bins in registers (L <= 256, L and ld multiples of
+// 4, G 16-byte aligned).  A warp walks a contiguous range of rows of one spin;
+// lane t holds the slots j = 128 c + 4 t + q (c < 2, q < 4) and loads
+// G[r][j .. j + 3] with one 16-byte load per c.  After row r slot j holds the
+// running sum of bin (r - j) mod L; from one row to the next every bin moves
+// from slot j to slot j + 1 (from L - 1 to 0), so a lane's four slots shift
+// by one register and the first takes the last of the lane below (lane 0:
+// slot 127 of lane 31, or slot L - 1) by shuffles, and no bin is read or
+// written in shared memory until the warp's range ends: one store per bin
+// into the warp's partial sums (part, pitch L).
+template <int RB>
+__device__ __forceinline__ void measure_rows_reg(const float* __restrict__ Gu, const float* __restrict__ Gd,
+                                                 int ld, int L, float* part) {
+  constexpr int NW = kDelNT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool two = L > 128;                    // slots of the second block of 128 columns in use
+  const int lastc = (L - 1) >> 7, lastl = ((L - 1) & 127) >> 2;  // slot L - 1 (its q is 3)
+  const int below = (lane + 31) & 31;
+  for (int sp = 0; sp < 2; ++sp) {
+    const float* G = sp ? Gd : Gu;
+    const int rb = (warp * L) / NW, re = ((warp + 1) * L) / NW;
+    float acc[2][4];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[c][q] = 0.f;
+    for (int r0 = rb; r0 < re; r0 += RB) {
+      float4 v[RB][2];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int r = r0 + b;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int j = 128 * c + 4 * lane;
+          v[b][c] = (r < re && j < L) ? *reinterpret_cast<const float4*>(G + (size_t)r * ld + j)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int r = r0 + b;
+        if (r >= re) break;  // warp-uniform
+        if (r > rb) {
+          // every bin one slot up
+          const float t0 = __shfl_sync(0xffffffffu, acc[0][3], below);
+          const float t1 = __shfl_sync(0xffffffffu, acc[1][3], below);
+          const float t2 = __shfl_sync(0xffffffffu, lastc ? acc[1][3] : acc[0][3], lastl);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            acc[c][3] = acc[c][2];
+            acc[c][2] = acc[c][1];
+            acc[c][1] = acc[c][0];
+          }
+          acc[0][0] = lane ? t0 : t2;
+          acc[1][0] = lane ? t1 : t0;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (c == 1 && !two) break;  // uniform
+          const int j = 128 * c + 4 * lane;
+          const float x[4] = {v[b][c].x, v[b][c].y, v[b][c].z, v[b][c].w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[c][q] += (r >= j + q) ? x[q] : -x[q];
+        }
+      }
+    }
+    // slot j holds bin (re - 1 - j) mod L of this warp's rows
+    float* pw = part + (size_t)(sp * NW + warp) * L;
+    if (re > rb) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 128 * c + 4 * lane + q;
+          if (j < L) {
+            int k = re - 1 - j;
+            k += k < 0 ? L : 0;
+            pw[k] = acc[c][q];
+          }
+        }
+    }
+  }
+}
+
 // Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l}, walked
 // row by row: element (r, l) belongs to k = r - l (sign +) or r - l + L
 // (sign -, antiperiodic wrap).  Each warp takes whole rows, lanes take
@@ -678,7 +762,10 @@ __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < 2 * NW * L; e += kDelNT) part[e] = 0.f;
   __syncthreads();
-  if (L <= 256) {
+  if (L <= 256 && L % 4 == 0 && ld % 4 == 0 &&
+      ((reinterpret_cast<uintptr_t>(Gu) | reinterpret_cast<uintptr_t>(Gd)) & 15) == 0) {
+    measure_rows_reg<4>(Gu, Gd, ld, L, part);
+  } else if (L <= 256) {
     measure_rows_batched<4, 8>(Gu, Gd, ld, L, part);
   } else if (L <= 512) {
     measure_rows_batched<2, 16>(Gu, Gd, ld, L, part);
