@@ -13,7 +13,10 @@ Printed (one JSON line, rank 0): value (device-timed, inputs resident),
 e2e (same metric through the C ABI from pinned host buffers, G0 upload and
 G(tau) download in the timed region), roofline of the sweep kernel,
 cpu_baseline (the FP64 oracle on the host cores, bounded sample), the FP64
-rank-1 GPU path on the same workload, and the FP32-vs-FP64 G(tau) error.
+rank-1 GPU path on the same workload, and the FP32-vs-FP64 G(tau) error of
+the benched configuration (g_tau_err_vs_fp64: per grid, the FP32 run's flips
+replayed by the FP64 rank-1 path, chain-paired difference of the measured
+G(tau), outside the timed region).
 
 --impl reference runs the oracle (the plain FP64 CPU HF-QMC) on the same
 workload shape as the reference arm.
@@ -203,6 +206,47 @@ def run_reference(args, rank, world):
 # -------------------------------------------------------------------------
 # our arm
 # -------------------------------------------------------------------------
+def paired_error(hfqmc, inputs, beta, grids, args, stream, n_warm=30, n_meas=470):
+    """Error of the benched FP32 configuration's G(tau) against FP64 on the
+    same trajectory: the FP32 run records its flips, the FP64 rank-1 run
+    replays them, and per grid the chain-paired difference of the measured
+    G(tau) gives max_k |mean_c d_c(tau_k)| and its paired standard error
+    (and the same for D).  Outside the timed region."""
+    S = n_warm + n_meas
+    ctx32, g0 = make_ctx(hfqmc, inputs, beta, grids, args.precision, args, stream, seed=1)
+    ctx32.set_trace("record", S)
+    ctx32.sweep(n_warm, n_meas)
+    chains = [g[3] for g in grids]
+    traces = [ctx32.get_trace(i, chains[i]) for i in range(len(grids))]
+    ctx64, _ = make_ctx(hfqmc, inputs, beta, grids, "f64_rank1", argparse.Namespace(
+        k=0, n_wrap=4096, flush="auto"), stream, seed=1)
+    ctx64.set_trace("replay", S)
+    for i in range(len(grids)):
+        ctx64.put_trace(i, traces[i])
+    ctx64.sweep(n_warm, n_meas)
+    out = []
+    for i, (_, _, L, nc) in enumerate(grids):
+        d = np.empty((nc, L))
+        dD = np.empty(nc)
+        same = True
+        for c in range(nc):
+            a, b = ctx32.get_chain(i, c), ctx64.get_chain(i, c)
+            same = same and a["hash"] == b["hash"]
+            d[c] = -((a["acc"][:L] + a["acc"][L:]) - (b["acc"][:L] + b["acc"][L:])) / (2.0 * n_meas)
+            dD[c] = (ctx32.get_chain_D(i, c)[0] - ctx64.get_chain_D(i, c)[0]) / n_meas
+        st = ctx32.get_stats(i)
+        mean, sig = d.mean(0), d.std(0, ddof=1) / np.sqrt(nc)
+        out.append({"L": L, "max_abs_dG": float(np.max(np.abs(mean))),
+                    "max_sigma_paired": float(np.max(sig)),
+                    "within_1e5_plus_3sigma": bool(np.all(np.abs(mean) <= 1e-5 + 3 * sig)),
+                    "dD": float(dD.mean()), "dD_sigma_paired": float(dD.std(ddof=1) / np.sqrt(nc)),
+                    "same_trajectory": bool(same), "sweeps": S,
+                    "recomputes_per_chain": st["recomputes"] / nc, "n_wrap": st["n_wrap"]})
+    ctx32.close()
+    ctx64.close()
+    return out
+
+
 def make_ctx(hfqmc, inputs, beta, grids, precision, args, stream, seed=1):
     U = [g[0] for g in grids]
     dtau = [g[1] for g in grids]
@@ -226,6 +270,11 @@ def run_ours(args, rank, world, local):
     w, grids = workload(args.workload)
     if args.chains:
         grids = [(U, dt, L, args.chains) for (U, dt, L, _) in grids]
+    # the workload's own delay depth / recompute interval unless overridden
+    if not args.k and w.get("k"):
+        args.k = int(w["k"])
+    if not args.n_wrap and w.get("n_wrap"):
+        args.n_wrap = int(w["n_wrap"])
     beta = w["beta"]
     stream = torch.cuda.Stream()
     pps = proposals_per_sweep(grids)
@@ -313,8 +362,8 @@ def run_ours(args, rank, world, local):
                                "sweeps": S64, "speedup_fp32_delayed": value / (pps * S64 / (ms64 * 1e-3))}
         ctx64.close()
         # the same FP32 delayed path with the FP64 recompute every 64 accepted
-        # flips (the configurations' own N_wrap), over a short run
-        Sw = max(10, S // 20)
+        # flips (the configurations' own N_wrap), one full-length step
+        Sw = S
         ctx_w, _ = make_ctx(hfqmc, inputs, beta, grids, "f32_delayed", argparse.Namespace(
             k=args.k, n_wrap=64, flush=args.flush), stream, seed=1)
         ctx_w.sweep(0, 1)
@@ -325,6 +374,7 @@ def run_ours(args, rank, world, local):
                                          "sweeps": Sw,
                                          "drift_max": max(st["drift_max"] for st in stw)}
         ctx_w.close()
+        extra["g_tau_err_vs_fp64"] = paired_error(hfqmc, inputs, beta, grids, args, stream)
         extra["cpu_baseline"] = oracle_sample(grids, beta, args.cpu_seconds)
     line = {"metric": "HS flip proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

@@ -4,9 +4,9 @@
  * The library solves the fixed-bath impurity problem of the paper's
  * "Multigrid HF-QMC method" section: for one bath Green function G0 it runs
  * Hirsch-Fye QMC on several imaginary-time grids dtau_i at once, with many
- * independent Markov chains per grid ("the raw Green functions G_dtau_i are
- * averaged over 10-20 impurity solutions"), and returns the measured G(tau)
- * with error bars per grid.  The dtau -> 0 extrapolation, Fourier transforms
+ * independent Markov chains per grid (the paper averages each grid's Green
+ * function over 10 to 20 independent impurity solutions), and returns the
+ * measured G(tau) with error bars per grid.  The dtau -> 0 extrapolation, Fourier transforms
  * and the DMFT self-consistency are host-side glue above this ABI.
  *
  * Method (introduction of the paper: Trotter slicing into Lambda = beta/dtau
@@ -131,6 +131,11 @@ typedef struct hfqmc_ctx hfqmc_ctx;
 void hfqmc_default_opts(hfqmc_opts *opts);
 
 /* Creates a context for one beta and one U over n_grids dtau grids.
+ * Paper: "Multigrid HF-QMC method" section -- the impurity problem for one
+ * bath is solved on several grids dtau_i at once (Lambda_i = beta/dtau_i
+ * slices each, the Trotter discretisation of the introduction), with 10-20
+ * independent impurity solutions per grid that are averaged; here each
+ * solution is one Markov chain and all chains of all grids share one launch.
  * dtau[i]: grid spacing; Lambda_i = beta/dtau_i must be an integer
  *          (|beta/dtau_i - Lambda_i| < 1e-9), 1 <= Lambda_i <= 1024.
  * chains_per_grid[i] >= 1 independent chains on grid i.
@@ -141,12 +146,18 @@ int hfqmc_create(hfqmc_ctx **out, double beta, double U, const double *dtau, int
                  const int *chains_per_grid, uint64_t seed, const hfqmc_opts *opts);
 
 /* As hfqmc_create, but grid i has its own interaction U[i] (several U values
- * batched in one launch); "grid" in every other call indexes these pairs. */
+ * batched in one launch); "grid" in every other call indexes these pairs.
+ * Paper: the same section, applied to the several U values of the
+ * "Benchmark results" runs (U = 4 ... 5.2) at once. */
 int hfqmc_create_ex(hfqmc_ctx **out, double beta, const double *U, const double *dtau,
                     int n_grids, const int *chains_per_grid, uint64_t seed,
                     const hfqmc_opts *opts);
 
-/* Sets the bath of grid `grid` from Lambda samples G0_tau[k] = G0(k dtau),
+/* Paper: the bath Green function G0 that the DMFT cycle hands to the impurity
+ * solver (Fig. 1, "Multigrid HF-QMC method": the same G0 for every grid),
+ * sampled on the grid, and the Hirsch-Fye Dyson equation that builds each
+ * chain's G from it.
+ * Sets the bath of grid `grid` from Lambda samples G0_tau[k] = G0(k dtau),
  * k = 0..Lambda-1, physical sign, G0_tau[0] = G0(0+) (host array, copied).
  * Builds the antiperiodic bath matrix M_ll' = -G0(tau_{l-l'}) (l >= l'),
  * +G0(tau_{l-l'+Lambda}) (l < l'), then for every chain of the grid computes
@@ -156,7 +167,11 @@ int hfqmc_create_ex(hfqmc_ctx **out, double beta, const double *U, const double 
  * bath and zero the measurement accumulators. */
 int hfqmc_set_G0(hfqmc_ctx *ctx, int grid, const double *G0_tau);
 
-/* Runs n_warm unmeasured then n_meas measured sweeps (one proposal per slice
+/* Paper: the Monte Carlo sampling of the binary Hubbard-Stratonovich field
+ * (introduction: flips of single slices s_l, cost proportional to dtau^-3),
+ * the hot path of the method; the measured G_dtau(tau) is the per-grid
+ * result that the multigrid section averages and extrapolates.
+ * Runs n_warm unmeasured then n_meas measured sweeps (one proposal per slice
  * l = 0..Lambda-1 in order per sweep) on every chain of every grid, as one
  * persistent launch over a longest-Lambda-first work queue.  Measured sweeps
  * accumulate g^sigma(tau_k) = (1/Lambda) sum_l sgn G^sigma_{(l+k) mod Lambda, l}
@@ -165,19 +180,28 @@ int hfqmc_set_G0(hfqmc_ctx *ctx, int grid, const double *G0_tau);
  * Requires hfqmc_set_G0 on every grid (HFQMC_ESTATE otherwise). */
 int hfqmc_sweep(hfqmc_ctx *ctx, int64_t n_warm, int64_t n_meas);
 
-/* Measured G(tau_k), k = 0..Lambda-1, and G(beta-) = -1 - G(0+) at index Lambda
+/* Paper: the per-grid result G_dtau_i(tau) averaged over the impurity
+ * solutions ("Multigrid HF-QMC method"), the input of the dtau -> 0
+ * extrapolation.
+ * Measured G(tau_k), k = 0..Lambda-1, and G(beta-) = -1 - G(0+) at index Lambda
  * (caller arrays of Lambda+1 doubles; G_err may be NULL).  Error: sample
  * standard deviation (n-1) of the chain means over sqrt(n_chains); for one
  * chain the measured sweeps of each hfqmc_sweep call are cut into 32
  * consecutive bins and the same estimator is applied to the bin means. */
 int hfqmc_get_G(hfqmc_ctx *ctx, int grid, double *G_tau, double *G_err);
 
-/* Double occupancy D = <n_up n_dn> and its error bar (same estimator). */
+/* Paper: the double occupancy D, the benchmark observable of the "Benchmark
+ * results" section (D versus dtau^2, Figs. 3-4), at fixed dtau.
+ * Double occupancy D = <n_up n_dn> and its error bar (same estimator). */
 int hfqmc_get_D(hfqmc_ctx *ctx, int grid, double *D, double *D_err);
 
+/* Per-grid counters of the sweeps (hfqmc_stats above): acceptance rate, flips,
+ * recomputes, drift, device time.  The paper quotes no such figure; the
+ * accept rate sets the work per proposal (the rank-1 update of the
+ * introduction's dtau^-3 cost runs once per accepted flip). */
 int hfqmc_get_stats(hfqmc_ctx *ctx, int grid, hfqmc_stats *out);
 
-/* Lambda of a grid. */
+/* Lambda = beta/dtau of a grid (the number of imaginary-time slices). */
 int hfqmc_grid_size(hfqmc_ctx *ctx, int grid, int *L);
 
 /* One chain's state, for parity tests: field s (Lambda int8), G^up and G^dn
@@ -189,6 +213,40 @@ int hfqmc_grid_size(hfqmc_ctx *ctx, int grid, int *L);
  * Any output pointer may be NULL. */
 int hfqmc_get_chain(hfqmc_ctx *ctx, int grid, int chain, int8_t *s, double *G_up,
                     double *G_dn, int64_t *counters, double *acc);
+
+/* One chain's double-occupancy sums, for parity tests: *D_sum = sum over the
+ * measured sweeps since the last hfqmc_set_G0 of (1/Lambda) sum_l n^up_l n^dn_l
+ * with n^sigma_l = 1 - G^sigma_ll ("Benchmark results": D at fixed dtau), and
+ * D_bins[32] the same sums per bin of each hfqmc_sweep call (as for G_err).
+ * Either pointer may be NULL. */
+int hfqmc_get_chain_D(hfqmc_ctx *ctx, int grid, int chain, double *D_sum, double *D_bins);
+
+/* ---- decision trace: FP32 against FP64 on the same trajectory ------------
+ * The paper has no counterpart; these calls state the error of the FP32
+ * paths' G(tau) against FP64 along one Markov trajectory.  Two runs with the
+ * same seed part ways at the first proposal whose FP32 and FP64 ratios fall
+ * on different sides of its uniform, after which their chains are
+ * independent; a trace fixes the trajectory instead.
+ * hfqmc_set_trace(ctx, mode, max_sweeps):
+ *   HFQMC_TRACE_RECORD: each later hfqmc_sweep (at most max_sweeps sweeps)
+ *     records, per chain and sweep, which slices it flipped (any precision);
+ *   HFQMC_TRACE_REPLAY: each later hfqmc_sweep takes its accept/reject
+ *     decisions from the trace (bit set = flip) instead of u < R; ratios,
+ *     flip factors, updates, recomputes and measurements run as usual (rank-1
+ *     paths only: HFQMC_EINVAL for F32_DELAYED);
+ *   HFQMC_TRACE_OFF: back to u < R.
+ *   The trace buffer (device memory of the context) holds, per grid, chains x
+ *   max_sweeps x ceil(Lambda/32) words: [chain][sweep][word], bit l % 32 of
+ *   word l / 32 for slice l, sweeps counted from the start of each
+ *   hfqmc_sweep call.  A call with more sweeps returns HFQMC_EINVAL.
+ * hfqmc_get_trace / hfqmc_put_trace copy one grid's words out of / into that
+ *   buffer (host arrays of exactly that many words, else HFQMC_EINVAL;
+ *   HFQMC_ESTATE without a trace).  Replaying a trace recorded by a context
+ *   with the same grids, chains, seed and bath reproduces its trajectory. */
+enum { HFQMC_TRACE_OFF = 0, HFQMC_TRACE_RECORD = 1, HFQMC_TRACE_REPLAY = 2 };
+int hfqmc_set_trace(hfqmc_ctx *ctx, int mode, int64_t max_sweeps);
+int hfqmc_get_trace(hfqmc_ctx *ctx, int grid, uint32_t *bits, int64_t n_words);
+int hfqmc_put_trace(hfqmc_ctx *ctx, int grid, const uint32_t *bits, int64_t n_words);
 
 /* ---- entry point that allocates nothing --------------------------------
  * The paper has no counterpart to this call; it exists for callers that may
@@ -215,13 +273,13 @@ int hfqmc_get_chain(hfqmc_ctx *ctx, int grid, int chain, int8_t *s, double *G_up
  * Memory: the bath matrix and the [A | M] workspace live in one file-scope
  * device array of 3 * HFQMC_NOALLOC_MAX_L^2 doubles (1.5 MiB) that every GPU
  * which loads the library holds until the process exits.  The call allocates
- * nothing (no cudaMalloc, no allocating library routine).  The first call on
- * a device looks up the array's device address once, with that device
- * current, so that first call should come before any stream capture.  Every
- * call uses the same array and leaves its contents behind (each call
- * overwrites what it reads); calls that overlap on the GPU -- from several
- * streams or threads at once -- race on it and must be serialised by the
- * caller. */
+ * nothing (no cudaMalloc, no allocating library routine).  Each call looks up
+ * the array's device address on the current device (cudaGetSymbolAddress),
+ * copies the status word back and synchronises cuda_stream before it returns,
+ * so no call of it can be captured in a CUDA graph.  Every call uses the same
+ * array and leaves its contents behind (each call overwrites what it reads);
+ * calls that overlap on the GPU -- from several streams or threads at once --
+ * race on it and must be serialised by the caller. */
 #define HFQMC_NOALLOC_MAX_L 256
 int hfqmc_green_noalloc(const double *G0_tau, const int8_t *s, int L, double dtau, double U,
                         double *G_up, double *G_dn, void *cuda_stream, int *status_out);

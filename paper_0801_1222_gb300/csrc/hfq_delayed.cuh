@@ -621,9 +621,11 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
 // them is used; the partial sums are then updated row after row (entries of
 // one row go to distinct k, entries of different rows may share one), so the
 // order of the additions is that of the plain row walk.
+// G is read with plain (coherent) loads: the same kernel writes it through
+// the flush's TMA reduce-adds, so the non-coherent read-only path that
+// const __restrict__ would allow is not valid here.
 template <int RB, int CPL>
-__device__ __forceinline__ void measure_rows_batched(const float* __restrict__ Gu,
-                                                     const float* __restrict__ Gd, int ld, int L,
+__device__ __forceinline__ void measure_rows_batched(const float* Gu, const float* Gd, int ld, int L,
                                                      float* part) {
   constexpr int NW = kDelNT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -674,8 +676,8 @@ __device__ __forceinline__ void measure_rows_batched(const float* __restrict__ G
 // written in shared memory until the warp's range ends: one store per bin
 // into the warp's partial sums (part, pitch L).
 template <int RB>
-__device__ __forceinline__ void measure_rows_reg(const float* __restrict__ Gu, const float* __restrict__ Gd,
-                                                 int ld, int L, float* part) {
+__device__ __forceinline__ void measure_rows_reg(const float* Gu, const float* Gd, int ld, int L,
+                                                 float* part) {
   constexpr int NW = kDelNT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool two = L > 128;                    // slots of the second block of 128 columns in use
@@ -747,13 +749,20 @@ __device__ __forceinline__ void measure_rows_reg(const float* __restrict__ Gu, c
   }
 }
 
-// Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l}, walked
-// row by row: element (r, l) belongs to k = r - l (sign +) or r - l + L
-// (sign -, antiperiodic wrap).  Each warp takes whole rows, lanes take
-// columns (coalesced), and accumulates into its own shared-memory row of
-// FP32 partial sums (no two lanes of a row share a k); the warps' partials
-// are added in a fixed order.  Everything stays on the FP32 pipe: the caller
-// folds the per-sweep totals into FP64 accumulators.
+// Measurement g^sigma(tau_k) = (1/L) sum_l sgn G^sigma_{(l+k) mod L, l} for G
+// in HBM, walked row by row: element (r, l) belongs to k = r - l (sign +) or
+// r - l + L (sign -, antiperiodic wrap).  Each warp takes rows, lanes take
+// columns (coalesced), and every warp's sums end in its own shared-memory row
+// of FP32 partial sums; the warps' partials are added in a fixed order.
+// Three walks, by Lambda and alignment:
+//  * measure_rows_reg (L <= 256, L and ld multiples of 4, G 16-byte aligned):
+//    a contiguous range of rows per warp with the bins in registers, one
+//    store per bin at the end;
+//  * measure_rows_batched (other L <= 512): batched loads, a shared-memory
+//    read-modify-write of the warp's partial row per element;
+//  * the plain row walk beyond.
+// Everything stays on the FP32 pipe: the caller folds the per-sweep totals
+// into FP64 accumulators.
 // part: 2 * NW * L floats of shared scratch; out[k], out[L+k] receive the
 // sums (not yet divided by L).
 __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, int L, float* part,

@@ -68,6 +68,8 @@ struct ItemPtrs {
   double* bins;   // 32 L
   double* accD;   // 1 + 32
   ChainCounters* cnt;
+  uint32_t* trace;  // decision trace of this chain: [sweep][ceil(L/32) words], bit l of a
+                    // sweep's words set iff slice l was flipped (null: no trace)
 };
 
 struct GridAccount {
@@ -93,7 +95,14 @@ struct SweepArgs {
   long long n_warm, n_meas;
   int accept_rule;           // 0 Metropolis, 1 heat bath
   int flush;                 // delayed path: 1 tcgen05, 2 FFMA
+  int trace_mode;            // 0 none, 1 record the accepted flips, 2 replay them (rank-1 paths)
+  int pad;
 };
+
+constexpr int kTraceOff = 0, kTraceRecord = 1, kTraceReplay = 2;
+
+// Words of one sweep's decision trace.
+__host__ __device__ inline int trace_words(int L) { return (L + 31) >> 5; }
 
 // Bytes of shared memory the FP64 recompute needs for its L x L workspace.
 __host__ __device__ inline size_t gj_smem_bytes(int L) { return (size_t)L * L * sizeof(double); }

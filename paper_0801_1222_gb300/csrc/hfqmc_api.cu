@@ -13,6 +13,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <cstdint>
 #include <string>
 #include <utility>
 #include <vector>
@@ -118,7 +119,22 @@ struct hfqmc_ctx {
   // sweep launch shape
   size_t sweep_smem = 0;
   int sweep_ctas = 0;
-  std::map<std::pair<long long, long long>, cudaGraphExec_t> graphs;
+  // instantiated graphs of hfqmc_sweep per (n_warm, n_meas), with the call
+  // stamp of their last use (at most kMaxGraphs kept; the least recently used
+  // one is destroyed first)
+  struct CachedGraph {
+    cudaGraphExec_t exec;
+    unsigned long long used;
+  };
+  std::map<std::pair<long long, long long>, CachedGraph> graphs;
+  unsigned long long graph_clock = 0;
+  // decision trace (hfqmc_set_trace): mode, sweeps per chain, device buffer
+  // and each grid's offset in it (words)
+  int trace_mode = 0;
+  long long trace_cap = 0;
+  uint32_t* d_trace = nullptr;
+  size_t trace_bytes = 0;
+  std::vector<size_t> trace_off;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_ms = 0.0;
   long long sweeps_done = 0;
@@ -158,6 +174,27 @@ void* dev_alloc(hfqmc_ctx* c, size_t bytes) {
   return p;
 }
 
+void dev_free(hfqmc_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      c->allocs.erase(c->allocs.begin() + (long)i);
+      break;
+    }
+  if (c->opts.alloc) {
+    if (c->opts.free) c->opts.free(p, c->opts.alloc_user);
+  } else {
+    cudaFree(p);
+  }
+}
+
+constexpr size_t kMaxGraphs = 8;
+
+void drop_graphs(hfqmc_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+}
+
 bool f64_path(const hfqmc_ctx* c) { return c->opts.precision == HFQMC_F64_RANK1; }
 size_t elem_size(const hfqmc_ctx* c) { return f64_path(c) ? sizeof(double) : sizeof(float); }
 
@@ -174,6 +211,8 @@ int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
   a.n_meas = n_meas;
   a.accept_rule = c->opts.accept_rule;
   a.flush = c->opts.flush;
+  a.trace_mode = c->trace_mode;
+  a.pad = 0;
   if (c->opts.precision == HFQMC_F32_DELAYED)
     return launch_sweep_delayed(a, c->sweep_ctas, c->sweep_smem, c->stream);
   return launch_sweep_rank1(f64_path(c), a, c->sweep_ctas, c->sweep_smem, c->stream);
@@ -183,6 +222,10 @@ int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
 int enqueue_sweep(hfqmc_ctx* c, long long n_warm, long long n_meas) {
   cudaError_t e = cudaMemsetAsync(c->d_queue, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(queue)");
+  if (c->trace_mode == kTraceRecord) {
+    e = cudaMemsetAsync(c->d_trace, 0, c->trace_bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(trace)");
+  }
   int r = launch_account(c->d_account, c->n_grids, n_meas, c->stream);
   if (r) return cuda_fail(c, (cudaError_t)r, "launch_account");
   r = launch_sweep_kernel(c, n_warm, n_meas);
@@ -487,6 +530,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
       p.bins = (double*)(c->d_pool + io[i].bins);
       p.accD = (double*)(c->d_pool + io[i].accD);
       p.cnt = (ChainCounters*)(c->d_pool + io[i].cnt);
+      p.trace = nullptr;
     }
   // longest-Lambda-first order (stable)
   std::vector<int> order(c->n_items);
@@ -608,11 +652,20 @@ int hfqmc_sweep(hfqmc_ctx* c, int64_t n_warm, int64_t n_meas) {
   for (int g = 0; g < c->n_grids; ++g)
     if (!c->gh[g].g0_set)
       return fail(c, HFQMC_ESTATE, "hfqmc_set_G0 has not been called for grid " + std::to_string(g));
+  if (c->trace_mode != kTraceOff && n_warm + n_meas > c->trace_cap)
+    return fail(c, HFQMC_EINVAL, "more sweeps than the decision trace holds (hfqmc_set_trace)");
   CK(cudaEventRecord(c->ev0, c->stream));
   if (c->opts.use_graph) {
     auto key = std::make_pair((long long)n_warm, (long long)n_meas);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
+      if (c->graphs.size() >= kMaxGraphs) {
+        auto lru = c->graphs.begin();
+        for (auto g = c->graphs.begin(); g != c->graphs.end(); ++g)
+          if (g->second.used < lru->second.used) lru = g;
+        cudaGraphExecDestroy(lru->second.exec);
+        c->graphs.erase(lru);
+      }
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       int r = enqueue_sweep(c, n_warm, n_meas);
@@ -623,9 +676,10 @@ int hfqmc_sweep(hfqmc_ctx* c, int64_t n_warm, int64_t n_meas) {
       cudaError_t e3 = cudaGraphInstantiate(&ex, graph, 0);
       cudaGraphDestroy(graph);
       if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
-      it = c->graphs.emplace(key, ex).first;
+      it = c->graphs.emplace(key, hfqmc_ctx::CachedGraph{ex, 0}).first;
     }
-    CK(cudaGraphLaunch(it->second, c->stream));
+    it->second.used = ++c->graph_clock;
+    CK(cudaGraphLaunch(it->second.exec, c->stream));
   } else {
     int r = enqueue_sweep(c, n_warm, n_meas);
     if (r) return r;
@@ -745,6 +799,100 @@ int hfqmc_get_chain(hfqmc_ctx* c, int grid, int chain, int8_t* s, double* G_up, 
   return HFQMC_OK;
 }
 
+int hfqmc_get_chain_D(hfqmc_ctx* c, int grid, int chain, double* D_sum, double* D_bins) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids) return fail(c, HFQMC_EINVAL, "grid out of range");
+  const GridHost& h = c->gh[grid];
+  if (chain < 0 || chain >= h.chains) return fail(c, HFQMC_EINVAL, "chain out of range");
+  const ItemPtrs& p = c->items[h.item0 + chain];
+  double buf[1 + kBins];
+  CK(cudaMemcpyAsync(buf, p.accD, sizeof(buf), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (D_sum) *D_sum = buf[0];
+  if (D_bins) std::memcpy(D_bins, buf + 1, sizeof(double) * kBins);
+  return HFQMC_OK;
+}
+
+int hfqmc_set_trace(hfqmc_ctx* c, int mode, int64_t max_sweeps) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (mode != HFQMC_TRACE_OFF && mode != HFQMC_TRACE_RECORD && mode != HFQMC_TRACE_REPLAY)
+    return fail(c, HFQMC_EINVAL, "unknown trace mode");
+  if (mode == HFQMC_TRACE_REPLAY && c->opts.precision == HFQMC_F32_DELAYED)
+    return fail(c, HFQMC_EINVAL, "replay runs on the rank-1 paths (F64_RANK1, F32_RANK1)");
+  if (mode != HFQMC_TRACE_OFF && (max_sweeps < 1 || max_sweeps > (1ll << 31)))
+    return fail(c, HFQMC_EINVAL, "max_sweeps must be in [1, 2^31]");
+  drop_graphs(c);  // the launch (kernel variant and its arguments) changes
+  if (mode == HFQMC_TRACE_OFF) {
+    for (auto& p : c->items) p.trace = nullptr;
+    c->trace_mode = kTraceOff;
+  } else {
+    std::vector<size_t> off(c->n_grids);
+    size_t words = 0;
+    for (int g = 0; g < c->n_grids; ++g) {
+      off[g] = words;
+      words += (size_t)c->gh[g].chains * (size_t)max_sweeps * trace_words(c->gh[g].L);
+    }
+    const size_t bytes = words * sizeof(uint32_t);
+    if (bytes > c->trace_bytes) {
+      CK(cudaStreamSynchronize(c->stream));
+      dev_free(c, c->d_trace);
+      c->d_trace = nullptr;
+      c->trace_bytes = 0;
+      c->d_trace = (uint32_t*)dev_alloc(c, bytes);
+      if (!c->d_trace) return fail(c, HFQMC_ENOMEM, "device allocation of the decision trace failed");
+      c->trace_bytes = bytes;
+    }
+    CK(cudaMemsetAsync(c->d_trace, 0, c->trace_bytes, c->stream));
+    c->trace_off = off;
+    c->trace_cap = max_sweeps;
+    for (int g = 0; g < c->n_grids; ++g)
+      for (int ch = 0; ch < c->gh[g].chains; ++ch)
+        c->items[c->gh[g].item0 + ch].trace =
+            c->d_trace + off[g] + (size_t)ch * (size_t)max_sweeps * trace_words(c->gh[g].L);
+    c->trace_mode = mode == HFQMC_TRACE_RECORD ? kTraceRecord : kTraceReplay;
+  }
+  CK(cudaMemcpyAsync(c->d_items, c->items.data(), sizeof(ItemPtrs) * c->n_items, cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HFQMC_OK;
+}
+
+// Shared checks of hfqmc_get_trace / hfqmc_put_trace; the grid's trace bytes
+// and device address on success.
+static int trace_span(hfqmc_ctx* c, int grid, int64_t n_words, size_t* bytes, uint32_t** dev) {
+  if (!c) return fail(nullptr, HFQMC_EINVAL, "ctx is NULL");
+  if (grid < 0 || grid >= c->n_grids) return fail(c, HFQMC_EINVAL, "grid out of range");
+  if (c->trace_mode == kTraceOff) return fail(c, HFQMC_ESTATE, "no decision trace (hfqmc_set_trace)");
+  const size_t w = (size_t)c->gh[grid].chains * (size_t)c->trace_cap * trace_words(c->gh[grid].L);
+  if (n_words < 0 || (size_t)n_words != w)
+    return fail(c, HFQMC_EINVAL, "n_words must be chains x max_sweeps x ceil(Lambda/32) = " + std::to_string(w));
+  *bytes = w * sizeof(uint32_t);
+  *dev = c->d_trace + c->trace_off[grid];
+  return HFQMC_OK;
+}
+
+int hfqmc_get_trace(hfqmc_ctx* c, int grid, uint32_t* bits, int64_t n_words) {
+  size_t bytes = 0;
+  uint32_t* dev = nullptr;
+  int r = trace_span(c, grid, n_words, &bytes, &dev);
+  if (r) return r;
+  if (!bits) return fail(c, HFQMC_EINVAL, "bits is NULL");
+  CK(cudaMemcpyAsync(bits, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HFQMC_OK;
+}
+
+int hfqmc_put_trace(hfqmc_ctx* c, int grid, const uint32_t* bits, int64_t n_words) {
+  size_t bytes = 0;
+  uint32_t* dev = nullptr;
+  int r = trace_span(c, grid, n_words, &bytes, &dev);
+  if (r) return r;
+  if (!bits) return fail(c, HFQMC_EINVAL, "bits is NULL");
+  CK(cudaMemcpyAsync(dev, bits, bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HFQMC_OK;
+}
+
 const char* hfqmc_last_error(const hfqmc_ctx* c) {
   return c ? c->err.c_str() : g_create_error.c_str();
 }
@@ -752,7 +900,7 @@ const char* hfqmc_last_error(const hfqmc_ctx* c) {
 void hfqmc_destroy(hfqmc_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  drop_graphs(c);
   for (void* p : c->allocs) {
     if (c->opts.alloc && c->opts.free)
       c->opts.free(p, c->opts.alloc_user);

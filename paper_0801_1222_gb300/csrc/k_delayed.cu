@@ -35,6 +35,9 @@ constexpr int kRowsPerThread = 2;  // rows t/2 + 256 q, q < 2: L <= 512
 constexpr int kRowStride = kDelNT / 2;
 constexpr int kNoSlice = 0x7fffffff;
 
+// kRecord: every accepted flip also sets its bit in the chain's decision
+// trace (a.trace_mode == kTraceRecord), for replay by an FP64 run.
+template <bool kRecord>
 __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   constexpr int NT = kDelNT;
   constexpr int NW = NT / 32;
@@ -283,6 +286,9 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
           }
         }
         hash = (hash ^ (unsigned long long)(t * (long long)L + l)) * kFnvPrime;
+        if constexpr (kRecord) {
+          if (tid == 0) ip.trace[(size_t)sw * trace_words(L) + (l >> 5)] |= 1u << (l & 31);
+        }
         ++n_acc;
         ++j;
         propose(l + 1);
@@ -385,10 +391,13 @@ size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int u
 }
 
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_delayed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_delayed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_delayed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_delayed, kDelNT, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_delayed<false>, kDelNT, smem);
   *threads = kDelNT;
   // each CTA holds kTmemCols of the SM's 512 TMEM columns for its lifetime
   *ctas_per_sm = occ < 512 / kTmemCols ? occ : 512 / kTmemCols;
@@ -396,7 +405,10 @@ int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
 }
 
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st) {
-  k_sweep_delayed<<<ctas, kDelNT, smem, st>>>(a);
+  if (a.trace_mode == kTraceRecord)
+    k_sweep_delayed<true><<<ctas, kDelNT, smem, st>>>(a);
+  else
+    k_sweep_delayed<false><<<ctas, kDelNT, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 

@@ -10,7 +10,6 @@
 // their own device buffers for the inputs and outputs; the bath matrix and
 // the Gauss-Jordan workspace live in the file-scope array below.
 #include <cmath>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -53,11 +52,6 @@ __global__ void __launch_bounds__(kNoAllocNT) k_green_noalloc(GridConst gc, cons
                                       false, status);
 }
 
-namespace {
-std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[64] = {nullptr};  // device address of the scratch, per device
-}  // namespace
-
 }  // namespace hfq
 
 extern "C" int hfqmc_green_noalloc(const double* G0_tau, const int8_t* s, int L, double dtau,
@@ -67,23 +61,16 @@ extern "C" int hfqmc_green_noalloc(const double* G0_tau, const int8_t* s, int L,
   if (L < 1 || L > kNoAllocMaxL) return HFQMC_EINVAL;
   if (!G0_tau || !s || !G_up || !G_dn) return HFQMC_EINVAL;
   if (!(dtau > 0.0) || !(U >= 0.0)) return HFQMC_EINVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HFQMC_ECUDA;
-  double* scratch;
-  {
-    // first call on this device: the host-side name of the array is not a
-    // device address; ask the runtime for it (with this device current)
-    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-        (void)cudaGetLastError();
-        return HFQMC_ECUDA;
-      }
-      g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_noalloc_ptr[dev];
+  // The host-side name of the array is not a device address: ask the runtime
+  // for the array's address on the current device, on every call (a cached
+  // address would outlive the context it belongs to after a device reset;
+  // the lookup costs little next to the L^3 elimination).
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    (void)cudaGetLastError();
+    return HFQMC_ECUDA;
   }
+  double* scratch = static_cast<double*>(p);
   GridConst gc = {};
   gc.L = L;
   gc.lambda = std::acosh(std::exp(0.5 * dtau * U));

@@ -112,7 +112,11 @@ __device__ __forceinline__ void flip_factors(const GridConst& gc, T gu, T gd, in
   }
 }
 
-template <typename T>
+// kTrace: kTraceRecord sets the bit of every accepted flip in the chain's
+// decision trace; kTraceReplay takes the decisions from the trace instead of
+// u < R (the flip ratios, flip factors and updates are computed as usual), so
+// that an FP64 run follows the trajectory another run recorded.
+template <typename T, int kTrace>
 __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a) {
   constexpr int NT = R1Traits<T>::NT;
   constexpr int NW = NT / 32;
@@ -200,6 +204,8 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
             const int l = w + lane;
             bool acc = false, bad = false;
             if (l < L) acc = decide<T>(gc, diag[l], diag[L + l], ss[l], us[l], a.accept_rule, &bad);
+            if constexpr (kTrace == kTraceReplay)
+              acc = l < L && ((ip.trace[(size_t)sw * trace_words(L) + (l >> 5)] >> (l & 31)) & 1u);
             const unsigned b = __ballot_sync(0xffffffffu, acc);
             const unsigned bb = __ballot_sync(0xffffffffu, bad);
             if (b) {
@@ -246,6 +252,9 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
         }
         if (tid == 0) ss[first] = (int8_t)(-sl);
         hash = (hash ^ (unsigned long long)(t * (long long)L + first)) * kFnvPrime;
+        if constexpr (kTrace == kTraceRecord) {
+          if (tid == 0) ip.trace[(size_t)sw * trace_words(L) + (first >> 5)] |= 1u << (first & 31);
+        }
         ++n_acc;
         __syncthreads();
         if (gc.n_wrap > 0 && --until_rec == 0) {
@@ -334,33 +343,45 @@ __global__ void __launch_bounds__(R1Traits<T>::NT, 1) k_sweep_rank1(SweepArgs a)
   }
 }
 
+template <typename T>
+static void launch_rank1_t(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st) {
+  constexpr int NT = R1Traits<T>::NT;
+  if (a.trace_mode == kTraceRecord)
+    k_sweep_rank1<T, kTraceRecord><<<ctas, NT, smem, st>>>(a);
+  else if (a.trace_mode == kTraceReplay)
+    k_sweep_rank1<T, kTraceReplay><<<ctas, NT, smem, st>>>(a);
+  else
+    k_sweep_rank1<T, kTraceOff><<<ctas, NT, smem, st>>>(a);
+}
+
 int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cudaStream_t st) {
-  if (f64) {
-    k_sweep_rank1<double><<<ctas, R1Traits<double>::NT, smem, st>>>(a);
-  } else {
-    k_sweep_rank1<float><<<ctas, R1Traits<float>::NT, smem, st>>>(a);
-  }
+  if (f64)
+    launch_rank1_t<double>(a, ctas, smem, st);
+  else
+    launch_rank1_t<float>(a, ctas, smem, st);
   return (int)cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t config_rank1_t(size_t smem, int* occ) {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_rank1<T, kTraceOff>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_rank1<T, kTraceRecord>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_rank1<T, kTraceReplay>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_sweep_rank1<T, kTraceOff>, R1Traits<T>::NT,
+                                                      smem);
+  return e;
+}
+
 int rank1_config(bool f64, size_t smem, int* threads, int* ctas_per_sm) {
-  cudaError_t e;
   int occ = 0;
-  if (f64) {
-    e = cudaFuncSetAttribute(k_sweep_rank1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_rank1<double>,
-                                                        R1Traits<double>::NT, smem);
-    *threads = R1Traits<double>::NT;
-  } else {
-    e = cudaFuncSetAttribute(k_sweep_rank1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_rank1<float>,
-                                                        R1Traits<float>::NT, smem);
-    *threads = R1Traits<float>::NT;
-  }
+  const cudaError_t e = f64 ? config_rank1_t<double>(smem, &occ) : config_rank1_t<float>(smem, &occ);
+  *threads = f64 ? R1Traits<double>::NT : R1Traits<float>::NT;
   *ctas_per_sm = occ;
   return (int)e;
 }

@@ -2,8 +2,8 @@
 //  * bath matrix M of a grid from its G0(tau_k) samples (antiperiodic Toeplitz);
 //  * per-chain initial field (Philox) and FP64 Gauss-Jordan Green matrices;
 //  * per-call measured-sweep bookkeeping;
-//  * per-grid mean over chains and error bars ("the raw Green functions are
-//    averaged over 10-20 impurity solutions", "Multigrid HF-QMC method" section).
+//  * per-grid mean over chains and error bars (the paper averages each grid's
+//    Green function over 10 to 20 impurity solutions, "Multigrid HF-QMC method").
 #include "hfq_device.cuh"
 #include "hfq_gj.cuh"
 #include "hfq_launch.h"

@@ -25,6 +25,8 @@ HFQMC_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "EDRIFT", -6: "ENUMERIC",
           -7: "ETIMEOUT"}
 PRECISION = {"f64_rank1": 0, "f32_rank1": 1, "f32_delayed": 2}
+TRACE = {"off": 0, "record": 1, "replay": 2}
+N_BINS = 32
 ACCEPT = {"metropolis": 0, "heat_bath": 1}
 FLUSH = {"auto": 0, "tcgen05": 1, "ffma": 2}
 
@@ -95,9 +97,14 @@ def load():
     lib.hfqmc_destroy.argtypes = [P]
     lib.hfqmc_destroy.restype = None
     lib.hfqmc_green_noalloc.argtypes = [P, P, I, D, D, P, P, P, ctypes.POINTER(I)]
+    lib.hfqmc_get_chain_D.argtypes = [P, I, I, P, P]
+    lib.hfqmc_set_trace.argtypes = [P, I, I64]
+    lib.hfqmc_get_trace.argtypes = [P, I, P, I64]
+    lib.hfqmc_put_trace.argtypes = [P, I, P, I64]
     for name in ("hfqmc_create", "hfqmc_create_ex", "hfqmc_set_G0", "hfqmc_sweep", "hfqmc_get_G",
                  "hfqmc_get_D", "hfqmc_get_stats", "hfqmc_grid_size", "hfqmc_get_chain",
-                 "hfqmc_green_noalloc"):
+                 "hfqmc_green_noalloc", "hfqmc_get_chain_D", "hfqmc_set_trace", "hfqmc_get_trace",
+                 "hfqmc_put_trace"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -187,6 +194,30 @@ def hfqmc_get_chain(ctx, grid, chain) -> dict:
     return dict(s=s, Gup=Gu, Gdn=Gd, proposals=int(cnt[0]), accepted=int(cnt[1]),
                 recomputes=int(cnt[2]), hash=int(np.array(cnt[3]).view(np.uint64)),
                 bad=int(cnt[4]), t=int(cnt[5]), acc=acc)
+
+
+def hfqmc_get_chain_D(ctx, grid, chain):
+    """(sum of D over the measured sweeps since set_G0, its 32 bin sums)."""
+    D = ctypes.c_double(0.0)
+    bins = np.empty(N_BINS)
+    _check(load().hfqmc_get_chain_D(ctx, grid, chain, ctypes.byref(D), _p(bins)), ctx)
+    return D.value, bins
+
+
+def hfqmc_set_trace(ctx, mode, max_sweeps):
+    """mode: "off", "record" or "replay" (see include/hfqmc.h)."""
+    _check(load().hfqmc_set_trace(ctx, TRACE[mode], int(max_sweeps)), ctx)
+
+
+def hfqmc_get_trace(ctx, grid, n_words):
+    bits = np.empty(int(n_words), dtype=np.uint32)
+    _check(load().hfqmc_get_trace(ctx, grid, _p(bits), int(n_words)), ctx)
+    return bits
+
+
+def hfqmc_put_trace(ctx, grid, bits):
+    b = np.ascontiguousarray(bits, dtype=np.uint32)
+    _check(load().hfqmc_put_trace(ctx, grid, _p(b), b.size), ctx)
 
 
 NOALLOC_MAX_L = 256
@@ -300,6 +331,25 @@ class HFQMC:
 
     def grid_size(self, grid):
         return hfqmc_grid_size(self.ctx, grid)
+
+    def get_chain_D(self, grid, chain):
+        return hfqmc_get_chain_D(self.ctx, grid, chain)
+
+    def set_trace(self, mode, max_sweeps=1):
+        hfqmc_set_trace(self.ctx, mode, max_sweeps)
+        self._trace_sweeps = int(max_sweeps)
+
+    def trace_words(self, grid, chains):
+        return chains * self._trace_sweeps * ((self.grid_size(grid) + 31) // 32)
+
+    def get_trace(self, grid, chains):
+        """One grid's trace as [chain][sweep][word] uint32."""
+        w = (self.grid_size(grid) + 31) // 32
+        return hfqmc_get_trace(self.ctx, grid, self.trace_words(grid, chains)).reshape(
+            chains, self._trace_sweeps, w)
+
+    def put_trace(self, grid, bits):
+        hfqmc_put_trace(self.ctx, grid, bits)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -52,5 +52,9 @@ def compare_chains(ctx, q, rel_tol=1e-10):
             assert err <= rel_tol * scale, (g, c, err)
             if och.n_meas:
                 assert np.max(np.abs(gc["acc"] - och.acc)) <= rel_tol * och.n_meas
+                # double occupancy summed over the measured sweeps ("Benchmark
+                # results": D at fixed dtau), each sweep's D <= 1/4
+                D_sum, _ = ctx.get_chain_D(g, c)
+                assert abs(D_sum - och.accD[0]) <= rel_tol * och.n_meas, (g, c, D_sum, och.accD[0])
             worst = max(worst, err / scale)
     return worst

@@ -62,3 +62,11 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(hfqmc, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         hfqmc.load()
+
+
+def test_trace_and_chain_calls_reject_a_null_context(lib):
+    so = lib.load()
+    assert so.hfqmc_set_trace(None, 1, 10) == -1
+    assert so.hfqmc_get_trace(None, 0, None, 0) == -1
+    assert so.hfqmc_put_trace(None, 0, None, 0) == -1
+    assert so.hfqmc_get_chain_D(None, 0, 0, None, None) == -1

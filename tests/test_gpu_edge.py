@@ -34,17 +34,23 @@ def test_tiny_grids_fp32_delayed(orc, L):
 
 
 def test_lambda_512_delayed_follows_oracle(orc):
+    """Lambda = 512 (two rows per thread): over a short run most chains
+    follow the oracle's decisions, and those that do hold G within the FP32
+    drift (at least two must, so the comparison cannot pass empty)."""
     beta = 51.2
-    ctx, q = make_pair(orc, beta, [(4.8, 0.1)], [1], precision="f32_delayed", n_wrap=-1,
+    ctx, q = make_pair(orc, beta, [(4.8, 0.1)], [4], precision="f32_delayed", n_wrap=-1,
                        drift_fail=1.0)
-    ctx.sweep(1, 0)
-    q.sweep(1, 0)
-    gc = ctx.get_chain(0, 0)
-    och = q.chains[0][0]
-    assert gc["accepted"] > 100
-    if gc["hash"] == och.decision_hash:
-        err = max(np.abs(gc["Gup"] - och.Gup).max(), np.abs(gc["Gdn"] - och.Gdn).max())
-        assert err < 1e-3
+    ctx.sweep(0, 1)
+    q.sweep(0, 1)
+    same = 0
+    for c, och in enumerate(q.chains[0]):
+        gc = ctx.get_chain(0, c)
+        assert gc["accepted"] > 100
+        if gc["hash"] == och.decision_hash:
+            same += 1
+            err = max(np.abs(gc["Gup"] - och.Gup).max(), np.abs(gc["Gdn"] - och.Gdn).max())
+            assert err < 1e-3
+    assert same >= 2
 
 
 def test_large_lambda_workload_shape_runs():

@@ -136,50 +136,31 @@ def test_tcgen05_flush_matches_ffma_flush():
         ctx.sweep(1, 0)
         out[flush] = [ctx.get_chain(g, c) for g in range(2) for c in range(2)]
         ctx.close()
+    same = 0
     for a, b in zip(out["ffma"], out["tcgen05"]):
         if a["hash"] == b["hash"]:
+            same += 1
             assert np.max(np.abs(a["Gup"] - b["Gup"])) < 1e-3
             assert np.max(np.abs(a["Gdn"] - b["Gdn"])) < 1e-3
+    assert same >= 2  # the comparison ran on at least half of the chains
 
 
-def test_G_tau_fp32_within_1e5_of_fp64():
-    """Same chains, same Philox stream: FP32 delayed vs FP64 rank-1 measured
-    G(tau) must differ by at most 1e-5 + 3 sigma (sigma of the difference)."""
+def test_G_tau_fp32_within_1e5_of_fp64_independent_chains():
+    """The statistical form of the criterion: FP32 delayed and FP64 rank-1
+    runs with the same seed (whose chains soon part ways) agree within
+    1e-5 + 3 sigma of the difference.  This bounds the FP32 path's total
+    effect -- its own decisions included -- at the statistical resolution;
+    tests/test_gpu_precision.py resolves the 1e-5 level on one trajectory."""
     from paper_0801_1222_gb300 import inputs
     h = lib()
     beta, U, L, nc = 20.0, 5.0, 100, 64
     g0 = inputs.bethe_G0_tau(beta, L)
     res = {}
     for prec in ("f64_rank1", "f32_delayed"):
-        ctx = h.HFQMC(beta, U, [beta / L], [nc], seed=11, precision=prec, n_wrap=256,
-                      drift_fail=1.0)
+        ctx = h.HFQMC(beta, U, [beta / L], [nc], seed=11, precision=prec, drift_fail=1.0)
         ctx.set_G0(0, g0)
         ctx.sweep(20, 200)
         res[prec] = ctx.get_G(0)
-        ctx.close()
-    G64, E64 = res["f64_rank1"]
-    G32, E32 = res["f32_delayed"]
-    sig = np.sqrt(E64 ** 2 + E32 ** 2)
-    assert np.all(np.abs(G32 - G64) <= 1e-5 + 3 * sig), np.max(np.abs(G32 - G64) / sig)
-
-
-def test_G_tau_tma_path_within_1e5_of_fp64():
-    """The same bound on the path that keeps G in HBM (Lambda = 160 at the
-    tuned k and N_wrap: TMA reduce flush, batched measurement walk)."""
-    from paper_0801_1222_gb300 import inputs
-    h = lib()
-    beta, U, L, nc = 32.0, 5.0, 160, 64
-    g0 = inputs.bethe_G0_tau(beta, L)
-    res = {}
-    for prec in ("f64_rank1", "f32_delayed"):
-        ctx = h.HFQMC(beta, U, [beta / L], [nc], seed=12, precision=prec, drift_fail=1.0,
-                      n_wrap=(1 << 30) if prec == "f64_rank1" else 0)
-        ctx.set_G0(0, g0)
-        ctx.sweep(20, 150)
-        res[prec] = ctx.get_G(0)
-        if prec == "f32_delayed":
-            st = ctx.get_stats(0)
-            assert st["k"] == 24  # G (206 KB) above the 200 KB on-chip budget: in HBM
         ctx.close()
     G64, E64 = res["f64_rank1"]
     G32, E32 = res["f32_delayed"]

@@ -1,0 +1,179 @@
+"""Error of the FP32 delayed path's G(tau) against FP64 on the same trajectory.
+
+The criterion: FP32 G(tau) within 1e-5 absolute of FP64 G(tau) on top of the
+statistical error.  Two runs with the same seed follow the same decisions only
+until the first proposal whose FP32 and FP64 flip ratios fall on different
+sides of its uniform; with the matrix drift of a long recompute interval that
+happens within a few hundred proposals, after which the chains are independent
+and their difference is pure statistics (about 1e-4 here), far too coarse to
+resolve 1e-5.  So the FP32 run records which slices it flipped
+(hfqmc_set_trace RECORD) and the FP64 rank-1 run replays exactly those flips:
+both measure G(tau) on one trajectory, and the per-chain difference of the
+measured G(tau) is the FP32 path's own error, paired chain by chain.
+
+For every tau_k the tests assert, over chains c with d_c(tau_k) = G32_c - G64_c
+(chain means over the measured sweeps):
+  sigma_paired = std(d) / sqrt(n_chains) <= 3e-6,
+  |mean(d)| <= 1e-5 + 3 sigma_paired,
+and the same for the double occupancy D.  The FP64 replay follows the
+recorded trajectory exactly (same decision hash and accept count per chain),
+and each run is long enough for several FP64 recomputes per chain at the
+recompute interval under test."""
+import numpy as np
+import pytest
+
+from gpu_common import lib
+
+pytestmark = pytest.mark.gpu
+
+SIG_MAX = 3e-6
+TOL = 1e-5
+
+
+def _chain_G(ctx, grid, chains, n_meas):
+    L = ctx.grid_size(grid)
+    out = np.empty((chains, L))
+    for c in range(chains):
+        acc = ctx.get_chain(grid, c)["acc"]
+        out[c] = -(acc[:L] + acc[L:]) / (2.0 * n_meas)
+    return out
+
+
+def paired_run(beta, grids, chains, seed, n_warm, n_meas, **kw32):
+    """FP32 delayed run that records its flips, FP64 rank-1 run that replays
+    them; per grid the paired statistics of G(tau) and D."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    U = [g[0] for g in grids]
+    dt = [g[1] for g in grids]
+    Ls = [int(round(beta / d)) for d in dt]
+    S = n_warm + n_meas
+    g0 = [inputs.bethe_G0_tau(beta, L) for L in Ls]
+    ctx32 = h.HFQMC(beta, U, dt, [chains] * len(grids), seed=seed, precision="f32_delayed",
+                    drift_fail=1.0, **kw32)
+    for i, g in enumerate(g0):
+        ctx32.set_G0(i, g)
+    ctx32.set_trace("record", S)
+    ctx32.sweep(n_warm, n_meas)
+    traces = [ctx32.get_trace(i, chains) for i in range(len(grids))]
+    ctx64 = h.HFQMC(beta, U, dt, [chains] * len(grids), seed=seed, precision="f64_rank1",
+                    n_wrap=4096, drift_fail=1.0)
+    for i, g in enumerate(g0):
+        ctx64.set_G0(i, g)
+    ctx64.set_trace("replay", S)
+    for i in range(len(grids)):
+        ctx64.put_trace(i, traces[i])
+    ctx64.sweep(n_warm, n_meas)
+    out = []
+    for i, L in enumerate(Ls):
+        for c in range(chains):
+            a, b = ctx32.get_chain(i, c), ctx64.get_chain(i, c)
+            assert a["hash"] == b["hash"] and a["accepted"] == b["accepted"], (L, c)
+            assert np.array_equal(a["s"], b["s"])
+        d = _chain_G(ctx32, i, chains, n_meas) - _chain_G(ctx64, i, chains, n_meas)
+        dD = np.array([ctx32.get_chain_D(i, c)[0] - ctx64.get_chain_D(i, c)[0]
+                       for c in range(chains)]) / n_meas
+        out.append(dict(L=L, mean=d.mean(0), sig=d.std(0, ddof=1) / np.sqrt(chains),
+                        Dmean=dD.mean(), Dsig=dD.std(ddof=1) / np.sqrt(chains),
+                        stats=ctx32.get_stats(i), trace=traces[i]))
+    ctx32.close()
+    ctx64.close()
+    return out
+
+
+def _assert_within(r, min_recomputes_per_chain):
+    st = r["stats"]
+    assert st["recomputes"] >= min_recomputes_per_chain * st["chains"], st
+    assert np.max(r["sig"]) <= SIG_MAX, (r["L"], np.max(r["sig"]))
+    assert np.all(np.abs(r["mean"]) <= TOL + 3 * r["sig"]), (r["L"], np.max(np.abs(r["mean"])))
+    assert r["Dsig"] <= SIG_MAX and abs(r["Dmean"]) <= TOL + 3 * r["Dsig"], (r["Dmean"], r["Dsig"])
+
+
+def test_trace_replay_reproduces_fp64_run(orc):
+    """A trace recorded by the FP64 rank-1 path and replayed by it reproduces
+    its own run bit for bit (decisions, G, measured G(tau)), and the replay
+    path takes the trace, not u < R: replaying an emptied trace flips nothing."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    beta, L = 10.0, 37
+    out = []
+    for mode in ("record", "replay"):
+        ctx = h.HFQMC(beta, 4.0, [beta / L], [3], seed=5, precision="f64_rank1", n_wrap=16)
+        ctx.set_G0(0, inputs.bethe_G0_tau(beta, L))
+        ctx.set_trace(mode, 12)
+        if mode == "replay":
+            ctx.put_trace(0, out[0][1])
+        ctx.sweep(2, 10)
+        out.append(([ctx.get_chain(0, c) for c in range(3)],
+                    ctx.get_trace(0, 3) if mode == "record" else None, ctx.get_G(0)[0]))
+        if mode == "record":
+            tr = out[0][1]
+            assert tr.shape == (3, 12, 2) and tr.any()
+            # the trace holds exactly the accepted flips
+            assert sum(int(np.unpackbits(tr[c].view(np.uint8)).sum()) for c in range(3)) == \
+                sum(ctx.get_chain(0, c)["accepted"] for c in range(3))
+        ctx.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert a["hash"] == b["hash"] and a["accepted"] == b["accepted"]
+        np.testing.assert_array_equal(a["Gup"], b["Gup"])
+        np.testing.assert_array_equal(a["acc"], b["acc"])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    ctx = h.HFQMC(beta, 4.0, [beta / L], [3], seed=5, precision="f64_rank1", n_wrap=16)
+    ctx.set_G0(0, inputs.bethe_G0_tau(beta, L))
+    ctx.set_trace("replay", 12)
+    ctx.sweep(2, 10)
+    assert ctx.get_stats(0)["accepted"] == 0
+    with pytest.raises(h.HFQMCError) as ei:
+        ctx.sweep(10, 10)  # more sweeps than the trace holds
+    assert ei.value.name == "EINVAL"
+    ctx.close()
+
+
+def test_trace_argument_checks():
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    ctx = h.HFQMC(8.0, 4.0, [0.5], [2], precision="f32_delayed")
+    ctx.set_G0(0, inputs.bethe_G0_tau(8.0, 16))
+    with pytest.raises(h.HFQMCError) as ei:
+        ctx.set_trace("replay", 4)  # the delayed path does not replay
+    assert ei.value.name == "EINVAL"
+    with pytest.raises(h.HFQMCError) as ei:
+        h.hfqmc_get_trace(ctx.ctx, 0, 8)  # no trace yet
+    assert ei.value.name == "ESTATE"
+    ctx.set_trace("record", 4)
+    with pytest.raises(h.HFQMCError) as ei:
+        h.hfqmc_get_trace(ctx.ctx, 0, 7)  # wrong size: 2 chains x 4 sweeps x 1 word
+    assert ei.value.name == "EINVAL"
+    ctx.sweep(1, 3)
+    ctx.set_trace("off")
+    ctx.sweep(5, 5)
+    ctx.close()
+
+
+def test_paired_G_tau_L100_shared_memory_path():
+    """Lambda = 100 (G on chip, k = 32) at the table's N_wrap 8192: about
+    36 flips per sweep, 700 sweeps, three recomputes per chain."""
+    r, = paired_run(20.0, [(5.0, 0.2)], 32, 11, 20, 680)
+    _assert_within(r, 2)
+
+
+def test_paired_G_tau_L160_L166_hbm_paths():
+    """Lambda = 160 (G in HBM, TMA reduce flush, register measurement walk)
+    and Lambda = 166 (G in HBM, Lambda % 4 != 0: per-thread flush adds and the
+    batched measurement walk) at the table's k and N_wrap 16384, past two
+    recomputes per chain."""
+    res = paired_run(32.0, [(5.0, 32.0 / 160), (5.0, 32.0 / 166)], 32, 12, 20, 580)
+    for r in res:
+        assert r["stats"]["k"] == 24
+        _assert_within(r, 2)
+
+
+def test_paired_G_tau_L200_L240_headline_grids():
+    """Lambda = 200 and 240, the grids that carry most of the multigrid
+    benchmark's work, at the benchmark's own settings (U = 5, beta = 40, k = 16,
+    N_wrap 16384, TMA reduce flush): 500 sweeps, two or more recomputes per
+    chain."""
+    res = paired_run(40.0, [(5.0, 40.0 / 200), (5.0, 40.0 / 240)], 32, 13, 30, 470)
+    for r in res:
+        assert r["stats"]["k"] == 16 and r["stats"]["n_wrap"] == 16384
+        _assert_within(r, 2)
