@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--flush", default="auto")
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--n-wrap", type=int, default=0)
+    ap.add_argument("--recompute", default="auto", choices=["auto", "gj", "refine"])
     ap.add_argument("--no-baselines", action="store_true", help="skip the oracle / FP64 legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--chains", type=int, default=0, help="override chains per grid (small cases)")
@@ -251,8 +252,9 @@ def make_ctx(hfqmc, inputs, beta, grids, precision, args, stream, seed=1):
     U = [g[0] for g in grids]
     dtau = [g[1] for g in grids]
     chains = [g[3] for g in grids]
+    rec = getattr(args, "recompute", "auto") if precision == "f32_delayed" else "auto"
     ctx = hfqmc.HFQMC(beta, U, dtau, chains, seed=seed, precision=precision, k=args.k,
-                      n_wrap=args.n_wrap, flush=args.flush, drift_fail=1.0, stream=stream)
+                      n_wrap=args.n_wrap, flush=args.flush, drift_fail=1.0, stream=stream, recompute=rec)
     g0 = [inputs.bethe_G0_tau(beta, g[2]) for g in grids]
     for i in range(len(grids)):
         ctx.set_G0(i, g0[i])
@@ -365,7 +367,7 @@ def run_ours(args, rank, world, local):
         # flips (the configurations' own N_wrap), one full-length step
         Sw = S
         ctx_w, _ = make_ctx(hfqmc, inputs, beta, grids, "f32_delayed", argparse.Namespace(
-            k=args.k, n_wrap=64, flush=args.flush), stream, seed=1)
+            k=args.k, n_wrap=64, flush=args.flush, recompute=args.recompute), stream, seed=1)
         ctx_w.sweep(0, 1)
         ctx_w.sweep(0, Sw)
         msw = ctx_w.get_stats(0)["last_sweep_ms"]

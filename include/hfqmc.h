@@ -102,7 +102,21 @@ typedef struct {
                               library copies it.  NULL / 0 entries: the built-in table.  An
                               autotuner that measures one is paper_0801_1222_gb300/autotune.py */
     int tune_entries;
+    int recompute;      /* F32_DELAYED: how G is rebuilt every n_wrap accepted flips.
+                           HFQMC_RECOMPUTE_AUTO (default) = REFINE for F32_DELAYED, GJ otherwise;
+                           HFQMC_RECOMPUTE_GJ: from the field, FP64 Gauss-Jordan inversion of
+                           G^{-1} = M^{-1}(1 + D) - D (by 16-column panels);
+                           HFQMC_RECOMPUTE_REFINE: one or two Newton steps G <- G + G (1 - G^{-1} G)
+                           from the current FP32 G, the residual formed from exact 7-bit integer
+                           slices of M^{-1} and G on the tensor cores (FP64-level accuracy of the
+                           residual), falling back to GJ when max |1 - G^{-1} G| > 2^-8 or for U = 0;
+                           the result is G to FP32 rounding.  EINVAL on the rank-1 paths. */
+    double refine_max;  /* REFINE: the largest max |1 - G^{-1} G| for which Newton steps are taken
+                           (0 = the default 2^-8; < 0 = never, every recompute from scratch);
+                           above 2^-13 a second step follows */
 } hfqmc_opts;
+
+enum { HFQMC_RECOMPUTE_AUTO = 0, HFQMC_RECOMPUTE_GJ = 1, HFQMC_RECOMPUTE_REFINE = 2 };
 
 /* Per-grid statistics (hfqmc_get_stats). */
 typedef struct {
@@ -118,6 +132,7 @@ typedef struct {
     double accept_rate;
     double drift_max;       /* max |G_fast - G_fresh| over recomputes since set_G0 */
     double last_sweep_ms;   /* device time of the last hfqmc_sweep (whole batch) */
+    int64_t recompute_fallbacks; /* recomputes the Newton refinement handed to Gauss-Jordan */
 } hfqmc_stats;
 
 typedef struct hfqmc_ctx hfqmc_ctx;

@@ -25,7 +25,9 @@ namespace hfq {
 
 constexpr int kDelNT = 512;          // threads per CTA (16 warps)
 constexpr int kUBlk = 2;             // U blocks of 128 rows staged (and multiplied) together
-constexpr int kTmemCols = 128 * kUBlk; // TMEM columns per CTA: one accumulator per staged U block
+// TMEM columns per CTA: the flush takes one 128-column accumulator per staged
+// U block, the recompute by Newton refinement (hfq_refine.cuh) up to 512
+constexpr int kTmemCols = 512;
 constexpr int kTileN = 128;          // output tile: 128 rows x 128 columns
 
 struct DelLayout {
@@ -35,10 +37,15 @@ struct DelLayout {
   // head: s (and, when the recompute works in shared memory, its scratch colk
   // and perm, which must survive the workspace overlaying the body; otherwise
   // they live in the idle staging area); body: stage, G, panels, diag
-  size_t off_colk, off_perm, off_s, off_body;
+  // (byte offsets in dynamic shared memory, below 227 KiB: 32 bits, which
+  // keeps the kernel's copy of the layout at one register per field)
+  uint32_t off_colk, off_perm, off_s, off_body;
   int ub;       // U blocks staged (and multiplied) together by the flush
-  size_t off_stage, off_G, off_U, off_W, off_diag, off_gtile, bytes;
-  size_t off_gjb;  // the recompute's panel scratch (workspace in HBM), overlaying all but G
+  uint32_t off_stage, off_G, off_U, off_W, off_diag, off_gtile;
+  size_t bytes;
+  uint32_t off_gjb;  // the recompute's panel scratch (workspace in HBM), overlaying all but G
+  uint32_t off_rf;   // the Newton refinement's staging (1024-aligned; overlays the whole body,
+                     // a resident G included: G is kept in HBM while it runs)
 };
 
 // product buffers of the TMA reduce flush: two halves of a tile, 64 rows x
@@ -69,14 +76,21 @@ __host__ __device__ inline size_t del_stage_bytes(int K, int L, int ub) {
   return (size_t)(2 + 2 * del_ublocks(L, ub)) * kTileN * KS * 2;
 }
 
+__host__ __device__ inline size_t rf_smem_need(int L) {
+  // rf_smem_bytes of hfq_refine.cuh: the larger of GEMM1's K chunk (A and H'
+  // slices) and GEMM2's (H' and E^T hi / lo parts)
+  const size_t g2 = (size_t)2 * 128 * kRf2KC * 2 + (size_t)2 * ((L + 15) / 16 * 16) * kRf2KC * 2;
+  return g2 > (size_t)kRfSmem ? g2 : (size_t)kRfSmem;
+}
+
 __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem,
-                                                bool gtile = false, int ub = kUBlk) {
+                                                bool gtile = false, int ub = kUBlk, bool refine = false) {
   DelLayout d;
   d.ldS = L | 1;
   d.KP = K + 4;  // 16-byte rows; (K+4) mod 32 spreads 8 rows of a 16-byte load over all banks
   d.KS = (K + 15) / 16 * 16;
   d.ub = del_ublocks(L, ub);
-  size_t o = 0;
+  size_t o = 0;  // offsets are computed in size_t and stored in 32 bits
   if (gj_smem) {
     d.off_colk = o;
     o += del_align((size_t)L * 8, 128);
@@ -119,6 +133,8 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   // G is resident (with the workspace in shared memory it is not used)
   d.off_gjb = resident ? del_align(d.off_U, 128) : del_align(d.off_body + scratch, 128);
   if (!gj_smem && d.off_gjb + gj_blocked_bytes(L) > o) o = d.off_gjb + gj_blocked_bytes(L);
+  d.off_rf = d.off_body;
+  if (refine && d.off_rf + rf_smem_need(L) > o) o = d.off_rf + rf_smem_need(L);
   d.bytes = o;
   return d;
 }
@@ -196,6 +212,9 @@ struct TcState {
   uint32_t mbar;       // shared address of the MMA completion mbarrier
   uint32_t phase;      // parity of the next MMA completion
   int failed;          // a wait gave up: the tensor path is not used again
+  uint32_t cbar;       // shared address of the refinement's mbarriers: bulk copy into
+                       // stage buffer 0, 1, then MMA completion of buffer 0, 1 (8 bytes apart)
+  uint32_t cphase;     // their parities (bit b of the barrier at cbar + 8 b)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -317,7 +336,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // Allocates kTmemCols TMEM columns (warp 0) and initialises the MMA
-// completion mbarrier s_mbar[0].
+// completion mbarrier s_mbar[0] and the refinement's four, s_mbar[1..4].
 __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long long* s_mbar,
                                 int* status) {
   (void)status;
@@ -329,7 +348,8 @@ __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long lon
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar)) : "memory");
+    for (int b = 0; b < 5; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar + b)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -339,6 +359,8 @@ __device__ inline void tc_setup(TcState* tc, uint32_t* s_tmem, unsigned long lon
   tc->mbar = smem_u32(s_mbar);
   tc->phase = 0;
   tc->failed = 0;
+  tc->cbar = smem_u32(s_mbar + 1);
+  tc->cphase = 0;
 }
 
 __device__ inline void tc_teardown(TcState* tc) {

@@ -27,6 +27,48 @@ constexpr int kStatusSingular = 1;   // zero pivot in a Gauss-Jordan recompute
 constexpr int kStatusNonFinite = 2;  // non-finite G after a recompute
 constexpr int kStatusTimeout = 4;    // a bounded wait gave up
 
+// ---------------------------------------------------------------------------
+// Newton refinement of G by exact sliced tensor-core products (the FP32
+// delayed path's recompute; see hfq_refine.cuh).  With D = diag(e^{sigma
+// lambda s} - 1), G^{-1} = B = M^{-1}(1 + D) - D = A (1 + D) with
+// A = M^{-1} - diag(1 - e^{-sigma lambda s_j}); the residual of G' is
+// E = 1 - B G' = 1 - A H', H' = (1 + D) G', and one step gives
+// G' + G' E = (1 + D)^{-1} (H' + H' E).  A and H' are cut into signed 7-bit
+// integer slices held exactly in FP16, so every slice product accumulates
+// exactly in the tensor cores' FP32 accumulators.
+// ---------------------------------------------------------------------------
+constexpr int kRfBits = 7;        // bits per slice
+constexpr int kRfSlicesA = 6;     // slices of A (42 bits)
+constexpr int kRfSlicesH = 4;     // slices of H' (28 bits)
+constexpr int kRfLevels = 6;      // products p + q = 0 .. 5 kept, one FP32 accumulator per level
+constexpr int kRfN = 64;          // columns of G per product tile
+constexpr int kRfKC = 32;         // K (contraction) extent of one staged chunk of the residual product
+constexpr int kRf2KC = 64;        // the same for the update product
+constexpr int kRfTileA = 128 * kRfKC * 2;        // bytes of one A slice of a (row block, K chunk)
+constexpr int kRfTileH = kRfN * kRfKC * 2;       // bytes of one H' slice of a (column block, K chunk)
+constexpr int kRfStage = kRfSlicesA * kRfTileA + kRfSlicesH * kRfTileH;  // 64 KiB: one chunk
+constexpr int kRfSmem = 2 * kRfStage;            // two stage buffers
+
+struct RefineConst {
+  const uint16_t* aslc;  // A's slices: [row block of 128][K chunk of 64][slice][128 x 64 FP16,
+                         // K-major core-matrix layout], padded with zeros
+  int ea;                // |A| < 2^ea (the slices' common scale)
+  int nrb, nkc;          // row blocks of 128, K chunks of 64 (Lambda padded)
+  float emax_step;       // Newton steps only while max |E| <= emax_step (else from scratch)
+  float cplus[2];        // e^{+lambda}, e^{-lambda} in FP32: (1 + d_j) for sigma s_j = +1, -1
+  float cminus_hi[2];    // e^{-sigma lambda s_j} = 1 / (1 + d_j) as an FP32 pair (hi + lo)
+  float cminus_lo[2];
+  uint16_t dslc[2][kRfSlicesA];  // slices (FP16 bits) of A_jj for sigma s_j = +1, -1
+};
+
+__host__ __device__ inline int rf_pad(int L, int m) { return (L + m - 1) / m * m; }
+// Bytes of A's slice table of one grid, and of the per-chain workspace the
+// refinement needs (E in FP32; the chain's FP64 Gauss-Jordan workspace has room).
+__host__ __device__ inline size_t rf_aslc_bytes(int L) {
+  return (size_t)(rf_pad(L, 128) / 128) * (rf_pad(L, kRfKC) / kRfKC) * kRfSlicesA * kRfTileA;
+}
+__host__ __device__ inline size_t rf_ws_bytes(int L) { return (size_t)L * L * 4; }
+
 struct GridConst {
   int L;           // Lambda
   int chains;
@@ -45,6 +87,7 @@ struct GridConst {
   const double* Minv; // its inverse (FP64, L x L), for the recompute through G^{-1}
   const void* tmapG;  // TMA tensor map (CUtensorMap, global memory) over the FP32 G of
                       // all chains: dims {column, row, spin, chain}; null unless gtile
+  const RefineConst* rc;  // recompute by Newton refinement (FP32 delayed path); null: Gauss-Jordan
 };
 
 struct ChainCounters {
@@ -56,7 +99,7 @@ struct ChainCounters {
   long long bad;             // proposals with R <= 0 or non-finite R
   double drift;              // max |G_fast - G_fresh| since the last set_G0
   int status;
-  int pad;
+  int fallbacks;             // recomputes that the refinement handed to Gauss-Jordan
 };
 
 struct ItemPtrs {
@@ -81,7 +124,7 @@ struct GridOut {
   long long proposals, accepted, recomputes, bad;
   double drift;
   double D, D_err;
-  double pad;
+  long long fallbacks;
 };
 
 struct SweepArgs {
@@ -96,7 +139,7 @@ struct SweepArgs {
   int accept_rule;           // 0 Metropolis, 1 heat bath
   int flush;                 // delayed path: 1 tcgen05, 2 FFMA
   int trace_mode;            // 0 none, 1 record the accepted flips, 2 replay them (rank-1 paths)
-  int pad;
+  int refine;                // delayed path: some grid recomputes by Newton refinement
 };
 
 constexpr int kTraceOff = 0, kTraceRecord = 1, kTraceReplay = 2;

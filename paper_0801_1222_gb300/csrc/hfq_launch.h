@@ -10,6 +10,9 @@ namespace hfq {
 // bath matrix M of one grid from G0(tau_k), and its FP64 inverse
 int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st);
 int launch_bath_inverse(int L, const double* M, double* Minv, int* status, cudaStream_t st);
+// slices of A = M^{-1} - diag(...) for the Newton refinement of G (FP32 delayed path)
+int launch_refine_prep(int L, const double* Minv, double lambda, RefineConst* rc, uint16_t* aslc,
+                       cudaStream_t st);
 // initial (or refreshed) field and Green matrices of the chains of one grid
 int launch_init_chains(const SweepArgs& a, const GridConst* d_grid_ptr, int item0, int n_chains,
                        int L, bool f64, bool first_time, bool gj_smem, cudaStream_t st);
@@ -28,7 +31,8 @@ int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cuda
 // delayed rank-k sweep (FP32); kDelayedTile: edge of the flush's output tiles
 // (the TMA reduce moves half a tile, kDelayedTile x kDelayedTile/2, at a time)
 constexpr int kDelayedTile = 128;
-size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile = false, int ub = 2);
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile = false, int ub = 2,
+                    bool refine = false);
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm);
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
 

@@ -34,6 +34,8 @@ thread_local std::string g_create_error;
 struct GridHost {
   double U, dtau, lambda;
   int L, chains, item0, k, n_wrap, resident, gj_smem, gtile = 0, ub = 2;
+  bool refine = false;  // recompute by Newton refinement (FP32 delayed path)
+  uint16_t* d_aslc = nullptr;  // its slice table of A (device)
   bool g0_set = false, ever_set = false;
   long long out_off;
 };
@@ -212,7 +214,9 @@ int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
   a.accept_rule = c->opts.accept_rule;
   a.flush = c->opts.flush;
   a.trace_mode = c->trace_mode;
-  a.pad = 0;
+  a.refine = 0;
+  for (int g = 0; g < c->n_grids; ++g)
+    if (c->gh[g].refine && c->gh[g].lambda != 0.0) a.refine = 1;
   if (c->opts.precision == HFQMC_F32_DELAYED)
     return launch_sweep_delayed(a, c->sweep_ctas, c->sweep_smem, c->stream);
   return launch_sweep_rank1(f64_path(c), a, c->sweep_ctas, c->sweep_smem, c->stream);
@@ -259,6 +263,10 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     return fail(nullptr, HFQMC_EINVAL, "unknown precision");
   if (o.accept_rule != HFQMC_METROPOLIS && o.accept_rule != HFQMC_HEAT_BATH)
     return fail(nullptr, HFQMC_EINVAL, "unknown accept_rule");
+  if (o.recompute < HFQMC_RECOMPUTE_AUTO || o.recompute > HFQMC_RECOMPUTE_REFINE)
+    return fail(nullptr, HFQMC_EINVAL, "unknown recompute method");
+  if (o.recompute == HFQMC_RECOMPUTE_REFINE && o.precision != HFQMC_F32_DELAYED)
+    return fail(nullptr, HFQMC_EINVAL, "the Newton refinement recompute belongs to the F32_DELAYED path");
   if (o.k != 0 && (o.k < 8 || o.k > 64 || o.k % 8 != 0))
     return fail(nullptr, HFQMC_EINVAL, "k must be 0 or a multiple of 8 in [8, 64]");
   std::vector<TuneEntry> user_table;
@@ -347,6 +355,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     // the delayed path always inverts its HBM workspace by panels
     h.gj_smem = o.precision != HFQMC_F32_DELAYED && o.gj_smem >= 0 &&
                 gj_smem_bytes(h.L) + 4 * (size_t)h.L * 8 + 1024 <= kSmemMax;
+    h.refine = o.precision == HFQMC_F32_DELAYED && o.recompute != HFQMC_RECOMPUTE_GJ;
     if (o.precision == HFQMC_F32_DELAYED) {
       if (h.L > 512) {
         g_create_error = "the delayed path handles Lambda <= 512 (two rows per thread)";
@@ -354,15 +363,15 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
         return HFQMC_EINVAL;
       }
       // the panels of both spins must fit in shared memory: lower k if needed
-      while (h.k > 8 && delayed_smem(h.L, h.k, false, h.gj_smem, false, 1) > kSmemMax) h.k -= 8;
-      if (delayed_smem(h.L, h.k, false, h.gj_smem, false, 1) > kSmemMax) {
+      while (h.k > 8 && delayed_smem(h.L, h.k, false, h.gj_smem, false, 1, h.refine) > kSmemMax) h.k -= 8;
+      if (delayed_smem(h.L, h.k, false, h.gj_smem, false, 1, h.refine) > kSmemMax) {
         g_create_error = "Lambda too large for the delayed path's shared-memory panels";
         hfqmc_destroy(c);
         return HFQMC_EINVAL;
       }
       // staging two U blocks per flush group when it fits, else one
-      h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2) <= kSmemMax ? 2 : 1;
-      sm = delayed_smem(h.L, h.k, true, h.gj_smem, false, h.ub);
+      h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2, h.refine) <= kSmemMax ? 2 : 1;
+      sm = delayed_smem(h.L, h.k, true, h.gj_smem, false, h.ub, h.refine);
       h.resident = sm <= kResidentBudget;
       h.gtile = 0;
       if (!h.resident) {
@@ -374,15 +383,15 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
             tensor_map_encoder() != nullptr) {
           for (int kt = h.k; kt >= 8 && !h.gtile; kt -= 8)
             for (int ub = 2; ub >= 1 && !h.gtile; --ub)
-              if (delayed_smem(h.L, kt, false, h.gj_smem, true, ub) <= kSmemMax) {
+              if (delayed_smem(h.L, kt, false, h.gj_smem, true, ub, h.refine) <= kSmemMax) {
                 h.k = kt;
                 h.ub = ub;
                 h.gtile = 1;
               }
         }
         if (!h.gtile)
-          h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2) <= kSmemMax ? 2 : 1;
-        sm = delayed_smem(h.L, h.k, false, h.gj_smem, h.gtile != 0, h.ub);
+          h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2, h.refine) <= kSmemMax ? 2 : 1;
+        sm = delayed_smem(h.L, h.k, false, h.gj_smem, h.gtile != 0, h.ub, h.refine);
       }
     } else {
       sm = rank1_smem(h.L, true, f64, h.gj_smem);
@@ -421,12 +430,17 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     off += align256(bytes);
     return o2;
   };
-  std::vector<size_t> offM(n_grids), offG0(n_grids), offMinv(n_grids);
+  std::vector<size_t> offM(n_grids), offG0(n_grids), offMinv(n_grids), offRc(n_grids), offAsl(n_grids);
   for (int g = 0; g < n_grids; ++g) {
     offM[g] = take(sizeof(double) * (size_t)c->gh[g].L * c->gh[g].L);
     offG0[g] = take(sizeof(double) * (size_t)c->gh[g].L);
   }
   for (int g = 0; g < n_grids; ++g) offMinv[g] = take(sizeof(double) * (size_t)c->gh[g].L * c->gh[g].L);
+  for (int g = 0; g < n_grids; ++g)
+    if (c->gh[g].refine) {
+      offRc[g] = take(sizeof(RefineConst));
+      offAsl[g] = take(rf_aslc_bytes(c->gh[g].L));
+    }
   struct ItemOff {
     size_t s, G, ws, acc, bins, accD, cnt;
   };
@@ -443,7 +457,8 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     int g = 0;
     while (g + 1 < n_grids && c->gh[g + 1].item0 <= i) ++g;
     const size_t L = c->gh[g].L;
-    io[i].ws = take(sizeof(double) * 2 * L * L);
+    const size_t ws = sizeof(double) * 2 * L * L;
+    io[i].ws = take(c->gh[g].refine && rf_ws_bytes((int)L) > ws ? rf_ws_bytes((int)L) : ws);
   }
   const size_t acc_begin = off;
   std::vector<size_t> acc_grid_begin(n_grids + 1);
@@ -482,10 +497,36 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     return bail(cuda_fail(c, e, "cudaMallocHost"));
   (void)acc_begin;
 
+  std::vector<RefineConst> rcs;
   for (int g = 0; g < n_grids; ++g) {
     c->gc[g].M = (const double*)(c->d_pool + offM[g]);
     c->gc[g].Minv = (const double*)(c->d_pool + offMinv[g]);
+    c->gc[g].rc = nullptr;
+    if (c->gh[g].refine) {
+      // the field-independent parts; ea and the slices come with each bath (set_G0)
+      const int L = c->gh[g].L;
+      const double lam = c->gh[g].lambda;
+      RefineConst r;
+      std::memset(&r, 0, sizeof(r));
+      c->gh[g].d_aslc = (uint16_t*)(c->d_pool + offAsl[g]);
+      r.aslc = c->gh[g].d_aslc;
+      r.nrb = (L + 127) / 128;
+      r.nkc = (L + kRfKC - 1) / kRfKC;
+      r.emax_step = o.refine_max == 0.0 ? 0.00390625f : (o.refine_max < 0.0 ? -1.f : (float)o.refine_max);
+      r.cplus[0] = (float)std::exp(lam);
+      r.cplus[1] = (float)std::exp(-lam);
+      for (int v = 0; v < 2; ++v) {
+        const double cm = std::exp(v == 0 ? -lam : lam);
+        r.cminus_hi[v] = (float)cm;
+        r.cminus_lo[v] = (float)(cm - (double)r.cminus_hi[v]);
+      }
+      RefineConst* dr = (RefineConst*)(c->d_pool + offRc[g]);
+      if ((e = cudaMemcpyAsync(dr, &r, sizeof(r), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
+      c->gc[g].rc = dr;
+    }
   }
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamSynchronize"));
   // tensor maps of the TMA reduce flush: the FP32 G of all chains of a grid,
   // dims {column, row, spin, chain} (the chains' G blocks are consecutive
   // takes of the pool, a constant stride apart), box 128 x 64 x 1 x 1 (half a
@@ -598,6 +639,7 @@ void hfqmc_default_opts(hfqmc_opts* o) {
   o->autotune = 1;
   o->flush = HFQMC_FLUSH_AUTO;
   o->use_graph = 1;
+  o->recompute = HFQMC_RECOMPUTE_AUTO;
 }
 
 int hfqmc_create(hfqmc_ctx** out, double beta, double U, const double* dtau, int n_grids,
@@ -626,6 +668,12 @@ int hfqmc_set_G0(hfqmc_ctx* c, int grid, const double* G0_tau) {
   // M^{-1} (closed form of a skew-circulant matrix) for the recompute through G^{-1}
   r = launch_bath_inverse(h.L, dM, const_cast<double*>(c->gc[grid].Minv), c->d_status, c->stream);
   if (r) return cuda_fail(c, (cudaError_t)r, "bath inverse kernel");
+  if (c->gc[grid].rc) {
+    // the refinement's slices of A = M^{-1} - diag(...) for this bath
+    RefineConst* rc = const_cast<RefineConst*>(c->gc[grid].rc);
+    r = launch_refine_prep(h.L, c->gc[grid].Minv, h.lambda, rc, h.d_aslc, c->stream);
+    if (r) return cuda_fail(c, (cudaError_t)r, "refinement slice kernel");
+  }
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.grids = c->d_grids;
@@ -748,6 +796,7 @@ int hfqmc_get_stats(hfqmc_ctx* c, int grid, hfqmc_stats* out) {
   out->accept_rate = o.proposals ? (double)o.accepted / (double)o.proposals : 0.0;
   out->drift_max = o.drift;
   out->last_sweep_ms = c->last_ms;
+  out->recompute_fallbacks = o.fallbacks;
   return HFQMC_OK;
 }
 

@@ -26,6 +26,7 @@
 #include "hfq_device.cuh"
 #include "hfq_gj.cuh"
 #include "hfq_launch.h"
+#include "hfq_refine.cuh"
 
 namespace hfq {
 
@@ -37,7 +38,11 @@ constexpr int kNoSlice = 0x7fffffff;
 
 // kRecord: every accepted flip also sets its bit in the chain's decision
 // trace (a.trace_mode == kTraceRecord), for replay by an FP64 run.
-template <bool kRecord>
+// kRefine: the recompute tries the Newton refinement (grids with a
+// RefineConst) before Gauss-Jordan; without it the kernel carries only the
+// Gauss-Jordan recompute (the refinement's code costs the accept loop some
+// registers, so contexts that never refine launch the variant without it).
+template <bool kRecord, bool kRefine>
 __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   constexpr int NT = kDelNT;
   constexpr int NW = NT / 32;
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   __shared__ int s_next[3];  // next accepted slice, triple-buffered (see take_next)
   __shared__ int s_bad;
   __shared__ uint32_t s_tmem_base;
-  __shared__ __align__(8) unsigned long long s_mbar[2];
+  __shared__ __align__(8) unsigned long long s_mbar[5];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool use_tc = a.flush != 2;
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     const GridConst gc = a.grids[ip.grid];
     const int L = gc.L, K = gc.k;
     const bool resident = gc.resident != 0;
-    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0, gc.ub);
+    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0, gc.ub, gc.rc != nullptr);
     // product tile buffer of the TMA reduce flush (G in HBM, tensor map set)
     float* dtile = gc.gtile ? reinterpret_cast<float*>(smem + lay.off_gtile) : nullptr;
 
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     // multiple of n_wrap); counted down so the hot loop needs no 64-bit modulo
     int until_rec = gc.n_wrap > 0 ? (int)(gc.n_wrap - n_acc % gc.n_wrap) : 0;
     long long n_rec = 0, n_bad = 0;
+    int n_fb = 0;  // recomputes the refinement handed to Gauss-Jordan
     unsigned long long hash = c0.hash;
     double drift = c0.drift;
     const long long n_sweeps = a.n_warm + a.n_meas;
@@ -303,11 +309,41 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         if (gc.n_wrap > 0 && --until_rec == 0) {
           until_rec = gc.n_wrap;
           flush();
-          // FP64 workspace in HBM, inverted by panels whose scratch overlays
-          // the idle part of shared memory (never G)
-          const double d = recompute_green_inv<float, NT, true>(
-              gc, ss, Gu, Gd, ld, ip.ws, red, redi, &s_inv, &s_piv, colk, perm, true, a.status, 0, 2,
-              reinterpret_cast<double*>(smem + lay.off_gjb));
+          double d = -1.0;
+          // G in HBM while the refinement runs (its staging overlays the whole
+          // body of shared memory, a resident G included)
+          bool in_hbm = false;
+          if (kRefine && gc.rc && use_tc && !tc.failed && gc.lambda != 0.0) {
+            if (resident) {
+              for (int i = warp; i < 2 * L; i += NW)
+                for (int jj = lane; jj < L; jj += 32) Ggl[(size_t)i * L + jj] = Gu[(size_t)i * ld + jj];
+              __syncthreads();
+              in_hbm = true;
+            }
+            int steps = 0;
+            float* rws = reinterpret_cast<float*>(ip.ws);
+            float* rred = reinterpret_cast<float*>(red);
+            const float d0 = refine_spin(gc, *gc.rc, ss, 1, Ggl, rws, smem + lay.off_rf, &tc, rred, a.status, &steps);
+            const float d1 = d0 >= 0.f ? refine_spin(gc, *gc.rc, ss, -1, Ggl + (size_t)L * L, rws, smem + lay.off_rf,
+                                                     &tc, rred, a.status, &steps)
+                                       : -1.f;
+            if (d0 >= 0.f && d1 >= 0.f)
+              d = fmax((double)d0, (double)d1);
+            else
+              ++n_fb;
+          }
+          if (d < 0.0) {
+            // from scratch: FP64 workspace in HBM, inverted by panels whose
+            // scratch overlays the idle part of shared memory (never G)
+            d = recompute_green_inv<float, NT, true>(
+                gc, ss, in_hbm ? Ggl : Gu, in_hbm ? Ggl + (size_t)L * L : Gd, in_hbm ? L : ld, ip.ws, red, redi,
+                &s_inv, &s_piv, colk, perm, true, a.status, 0, 2, reinterpret_cast<double*>(smem + lay.off_gjb));
+          }
+          if (in_hbm) {
+            for (int i = warp; i < 2 * L; i += NW)
+              for (int jj = lane; jj < L; jj += 32) Gu[(size_t)i * ld + jj] = Ggl[(size_t)i * L + jj];
+            __syncthreads();
+          }
           drift = fmax(drift, d);
           ++n_rec;
           zero_panels();  // the recompute's workspace may have overlaid them
@@ -379,6 +415,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       c.hash = hash;
       c.bad = c0.bad + n_bad;
       c.drift = drift;
+      c.fallbacks = c0.fallbacks + n_fb;
       *ip.cnt = c;
     }
     __syncthreads();
@@ -386,18 +423,18 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   if (use_tc) tc_teardown(&tc);
 }
 
-size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int ub) {
-  return del_layout(L, k, resident, gj_smem, gtile, ub).bytes;
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int ub, bool refine) {
+  return del_layout(L, k, resident, gj_smem, gtile, ub, refine).bytes;
 }
 
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_delayed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sweep_delayed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaSuccess;
+  for (auto* f : {k_sweep_delayed<false, false>, k_sweep_delayed<true, false>, k_sweep_delayed<false, true>,
+                  k_sweep_delayed<true, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_delayed<false>, kDelNT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_delayed<false, true>, kDelNT, smem);
   *threads = kDelNT;
   // each CTA holds kTmemCols of the SM's 512 TMEM columns for its lifetime
   *ctas_per_sm = occ < 512 / kTmemCols ? occ : 512 / kTmemCols;
@@ -405,10 +442,11 @@ int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
 }
 
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st) {
-  if (a.trace_mode == kTraceRecord)
-    k_sweep_delayed<true><<<ctas, kDelNT, smem, st>>>(a);
+  const bool rec = a.trace_mode == kTraceRecord;
+  if (a.refine)
+    (rec ? k_sweep_delayed<true, true> : k_sweep_delayed<false, true>)<<<ctas, kDelNT, smem, st>>>(a);
   else
-    k_sweep_delayed<false><<<ctas, kDelNT, smem, st>>>(a);
+    (rec ? k_sweep_delayed<true, false> : k_sweep_delayed<false, false>)<<<ctas, kDelNT, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 

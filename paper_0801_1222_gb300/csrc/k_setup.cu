@@ -4,6 +4,8 @@
 //  * per-call measured-sweep bookkeeping;
 //  * per-grid mean over chains and error bars (the paper averages each grid's
 //    Green function over 10 to 20 impurity solutions, "Multigrid HF-QMC method").
+#include <cuda_fp16.h>
+
 #include "hfq_device.cuh"
 #include "hfq_gj.cuh"
 #include "hfq_launch.h"
@@ -104,6 +106,79 @@ int launch_bath_inverse(int L, const double* M, double* Minv, int* status, cudaS
   return (int)cudaGetLastError();
 }
 
+// Slices of A = M^{-1} - diag(1 - e^{-sigma lambda s_j}) for the Newton
+// refinement (hfq_refine.cuh): every entry x of M^{-1} (padded with zeros to
+// whole 128-row blocks and 64-column chunks) is written as
+//   x = 2^ea sum_{p<6} s_p 2^{-7(p+1)} + (remainder below 2^{ea-43}),
+// s_p = rint of the running remainder times 2^7 (|s_0| <= 128, |s_p| <= 64),
+// each an integer held exactly in FP16, stored in the K-major core-matrix
+// layout the tensor-core operand wants (rows of A = M dimension, columns =
+// K).  A_jj depends on the chain's field: its two values are sliced into
+// rc->dslc and patched in per chain; ea covers both.  One block per (row
+// block, K chunk); every block finds the same ea.
+__device__ __forceinline__ uint32_t rf_core_offset(int r, int m) {
+  return (uint32_t)((r >> 3) * (kRfKC / 8) * 128 + (m >> 3) * 128 + (r & 7) * 16 + (m & 7) * 2);
+}
+
+__device__ __forceinline__ void rf_slice6(double x, int ea, float* q) {
+  double y = ldexp(x, kRfBits - ea);
+#pragma unroll
+  for (int p = 0; p < kRfSlicesA; ++p) {
+    const double r = rint(y);
+    q[p] = (float)r;
+    y = (y - r) * (double)(1 << kRfBits);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_refine_prep(int L, const double* __restrict__ Minv, double lambda,
+                                                     RefineConst* rc, uint16_t* __restrict__ aslc, int nkc) {
+  __shared__ double red[8];
+  const int tid = threadIdx.x;
+  const double a0 = Minv[0] - (1.0 - exp(-lambda)), a1 = Minv[0] - (1.0 - exp(lambda));
+  double m = fmax(fabs(a0), fabs(a1));
+  for (int d = tid; d < L; d += 256) m = fmax(m, fabs(Minv[(size_t)d * L]));  // c'(d), all d
+  m = block_max<256>(m, red);
+  int ea = 0;
+  if (m > 0.0) (void)frexp(m, &ea);  // m < 2^ea
+  if (blockIdx.x == 0 && tid == 0) {
+    rc->ea = ea;
+    float q[kRfSlicesA];
+    rf_slice6(a0, ea, q);
+    for (int p = 0; p < kRfSlicesA; ++p) rc->dslc[0][p] = __half_as_ushort(__float2half_rn(q[p]));
+    rf_slice6(a1, ea, q);
+    for (int p = 0; p < kRfSlicesA; ++p) rc->dslc[1][p] = __half_as_ushort(__float2half_rn(q[p]));
+  }
+  const int rb = blockIdx.x / nkc, kc = blockIdx.x - rb * nkc;
+  uint16_t* tile = aslc + (size_t)blockIdx.x * kRfSlicesA * (kRfTileA / 2);
+  for (int c = tid; c < 128 * (kRfKC / 8); c += 256) {
+    const int r = c / (kRfKC / 8), m0 = (c - r * (kRfKC / 8)) * 8;
+    const int i = rb * 128 + r;
+    uint32_t w[kRfSlicesA][4];
+#pragma unroll
+    for (int t = 0; t < 8; t += 2) {
+      const int j = kc * kRfKC + m0 + t;
+      float q0[kRfSlicesA], q1[kRfSlicesA];
+      rf_slice6(i < L && j < L ? Minv[(size_t)i * L + j] : 0.0, ea, q0);
+      rf_slice6(i < L && j + 1 < L ? Minv[(size_t)i * L + j + 1] : 0.0, ea, q1);
+#pragma unroll
+      for (int p = 0; p < kRfSlicesA; ++p)
+        w[p][t / 2] = (uint32_t)__half_as_ushort(__float2half_rn(q0[p])) |
+                      ((uint32_t)__half_as_ushort(__float2half_rn(q1[p])) << 16);
+    }
+    const uint32_t off = rf_core_offset(r, m0) / 2;
+#pragma unroll
+    for (int p = 0; p < kRfSlicesA; ++p)
+      *reinterpret_cast<uint4*>(tile + (size_t)p * (kRfTileA / 2) + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+}
+
+int launch_refine_prep(int L, const double* Minv, double lambda, RefineConst* rc, uint16_t* aslc,
+                       cudaStream_t st) {
+  const int nrb = rf_pad(L, 128) / 128, nkc = rf_pad(L, kRfKC) / kRfKC;
+  k_refine_prep<<<nrb * nkc, 256, 0, st>>>(L, Minv, lambda, rc, aslc, nkc);
+  return (int)cudaGetLastError();
+}
+
 // Initial (or, after a new bath, rebuilt) Green matrices of every chain of a
 // grid: block (chain, spin), so the two spins of a chain are inverted by two
 // CTAs at once.  The spin-up block also resets the chain's accumulators.
@@ -155,7 +230,7 @@ __global__ void __launch_bounds__(256) k_init_chains(SweepArgs a, const GridCons
       c.hash = kFnvOffset;
       c.bad = 0;
       c.status = 0;
-      c.pad = 0;
+      c.fallbacks = 0;
     } else {
       c = *ip.cnt;
     }
@@ -261,7 +336,7 @@ __global__ void __launch_bounds__(256) k_reduce(const GridConst* grids, const It
     oG[L] = -1.0 - oG[0];
     oE[L] = oE[0];
     GridOut o;
-    o.proposals = o.accepted = o.recomputes = o.bad = 0;
+    o.proposals = o.accepted = o.recomputes = o.bad = o.fallbacks = 0;
     o.drift = 0.0;
     for (int c = 0; c < nc; ++c) {
       const ChainCounters cc = *items[i0 + c].cnt;
@@ -269,6 +344,7 @@ __global__ void __launch_bounds__(256) k_reduce(const GridConst* grids, const It
       o.accepted += cc.accepted;
       o.recomputes += cc.recomputes;
       o.bad += cc.bad;
+      o.fallbacks += cc.fallbacks;
       o.drift = fmax(o.drift, cc.drift);
     }
     o.D = nan;
@@ -304,7 +380,6 @@ __global__ void __launch_bounds__(256) k_reduce(const GridConst* grids, const It
         }
       }
     }
-    o.pad = 0.0;
     gout[g] = o;
   }
 }

@@ -29,6 +29,7 @@ TRACE = {"off": 0, "record": 1, "replay": 2}
 N_BINS = 32
 ACCEPT = {"metropolis": 0, "heat_bath": 1}
 FLUSH = {"auto": 0, "tcgen05": 1, "ffma": 2}
+RECOMPUTE = {"auto": 0, "gj": 1, "refine": 2}
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -48,7 +49,8 @@ class hfqmc_opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("flush", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_user", ctypes.c_void_p),
                 ("resident_kb", ctypes.c_int), ("gj_smem", ctypes.c_int), ("gtile", ctypes.c_int),
-                ("tune_table", ctypes.POINTER(ctypes.c_int)), ("tune_entries", ctypes.c_int)]
+                ("tune_table", ctypes.POINTER(ctypes.c_int)), ("tune_entries", ctypes.c_int),
+                ("recompute", ctypes.c_int), ("refine_max", ctypes.c_double)]
 
 
 class hfqmc_stats(ctypes.Structure):
@@ -57,7 +59,7 @@ class hfqmc_stats(ctypes.Structure):
                 ("proposals", ctypes.c_int64), ("accepted", ctypes.c_int64),
                 ("recomputes", ctypes.c_int64), ("numeric_errors", ctypes.c_int64),
                 ("accept_rate", ctypes.c_double), ("drift_max", ctypes.c_double),
-                ("last_sweep_ms", ctypes.c_double)]
+                ("last_sweep_ms", ctypes.c_double), ("recompute_fallbacks", ctypes.c_int64)]
 
 
 _lib = None
@@ -275,7 +277,7 @@ class HFQMC:
     def __init__(self, beta, U, dtau, chains_per_grid, seed=1, precision="f32_delayed", k=0,
                  n_wrap=0, accept_rule="metropolis", drift_fail=1e-1, flush="auto",
                  use_graph=True, stream=None, torch_alloc=True, resident_kb=0, gj_smem=0,
-                 gtile=0, tune=None, autotune=True):
+                 gtile=0, tune=None, autotune=True, recompute="auto", refine_max=0.0):
         o = hfqmc_default_opts()
         o.precision = PRECISION[precision]
         o.k = int(k)
@@ -288,6 +290,8 @@ class HFQMC:
         o.gj_smem = int(gj_smem)
         o.gtile = int(gtile)
         o.autotune = 1 if autotune else 0
+        o.recompute = RECOMPUTE[recompute]
+        o.refine_max = float(refine_max)
         if tune is not None:  # [(Lambda_max, k, n_wrap), ...] (see autotune.py)
             flat = [int(v) for e in tune for v in e]
             self._tune = (ctypes.c_int * len(flat))(*flat)

@@ -64,7 +64,7 @@ def test_delayed_hbm_recompute_by_panels(orc):
     against the FP32 G; the drift stays at the FP32 level of 32 flips, and G
     follows the oracle wherever the decisions agree."""
     ctx, q = make_pair(orc, 20.0, [(5.0, 0.1)], [2], precision="f32_delayed", n_wrap=32,
-                       drift_fail=1.0)
+                       drift_fail=1.0, recompute="gj")
     ctx.sweep(1, 1)
     q.sweep(1, 1)
     st = ctx.get_stats(0)
