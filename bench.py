@@ -37,7 +37,9 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
-TRAFFIC_PER_1000_SWEEPS = 0.395566080e9 + 17.330203392e9  # dram read + write of one launch (ncu)
+# the earlier per-Lambda table with long recompute intervals, for comparison
+LONG_NWRAP_TABLE = [(64, 32, 8192), (128, 32, 8192), (144, 32, 16384), (176, 24, 16384), (1024, 16, 16384)]
+TRAFFIC_PER_1000_SWEEPS = None  # dram read + write of one launch (ncu), set when captured for this kernel
 
 
 def parse():
@@ -253,8 +255,10 @@ def make_ctx(hfqmc, inputs, beta, grids, precision, args, stream, seed=1):
     dtau = [g[1] for g in grids]
     chains = [g[3] for g in grids]
     rec = getattr(args, "recompute", "auto") if precision == "f32_delayed" else "auto"
+    tune = getattr(args, "tune", None) if precision == "f32_delayed" else None
     ctx = hfqmc.HFQMC(beta, U, dtau, chains, seed=seed, precision=precision, k=args.k,
-                      n_wrap=args.n_wrap, flush=args.flush, drift_fail=1.0, stream=stream, recompute=rec)
+                      n_wrap=args.n_wrap, flush=args.flush, drift_fail=1.0, stream=stream, recompute=rec,
+                      tune=tune)
     g0 = [inputs.bethe_G0_tau(beta, g[2]) for g in grids]
     for i in range(len(grids)):
         ctx.set_G0(i, g0[i])
@@ -307,19 +311,24 @@ def run_ours(args, rank, world, local):
     lib_ms = stats[0]["last_sweep_ms"]
 
     # roofline of the sweep kernel: algorithmic work = 4 Lambda^2 flops per
-    # accepted flip (the rank-1-equivalent update of both spins), timed by the
-    # library's events around the persistent launch (the other three launches
-    # of a step are < 0.1% of it)
-    acc_per_step = sum(st["accept_rate"] * g[2] * g[3] * S for st, g in zip(stats, grids))
-    flops_step = sum(st["accept_rate"] * g[2] * g[3] * S * 4.0 * g[2] ** 2
-                     for st, g in zip(stats, grids))
+    # accepted flip (the rank-1-equivalent update of both spins) plus
+    # (16/3) Lambda^3 per recompute (the LU solve of the Dyson equation for
+    # both spins, every n_wrap accepted flips), timed by CUDA events around
+    # each step (the other launches of a step are < 0.1% of it)
+    acc_step = [st["accept_rate"] * g[2] * g[3] * S for st, g in zip(stats, grids)]
+    upd_flops = sum(a * 4.0 * g[2] ** 2 for a, g in zip(acc_step, grids))
+    rec_flops = sum(a / st["n_wrap"] * (16.0 / 3.0) * g[2] ** 3 if st["n_wrap"] > 0 else 0.0
+                    for a, st, g in zip(acc_step, stats, grids))
+    flops_step = upd_flops + rec_flops
     pk, pk_kind = peaks()
-    # the flush contracts FP16 operands: the FP16 dense rate equals the BF16
-    # one (nominal ratio 1), so the measured BF16 burst figure is the peak
+    # the flush and the recompute's products contract FP16 operands: the FP16
+    # dense rate equals the BF16 one (nominal ratio 1), so the measured BF16
+    # burst figure is the peak
     f16_peak = pk["bf16_tflops"]
     achieved = flops_step / (statistics.median(step_ms) * 1e-3) / 1e12
     # DRAM bytes of one full-size launch (1000 sweeps of this workload), from
-    # the ncu capture summarised in profiles/k_sweep_delayed_multigrid.md
+    # the ncu capture summarised under profiles/ (None until recaptured for
+    # the current kernel)
     traffic = TRAFFIC_PER_1000_SWEEPS if (TRAFFIC_PER_1000_SWEEPS and args.workload == "multigrid_L100_240" and S == 1000
                                           and args.precision == "f32_delayed" and not args.chains
                                           and not args.k and not args.n_wrap) else None
@@ -327,9 +336,9 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "tensor", "achieved": achieved, "peak": f16_peak, "unit": "TFLOP/s",
                 "frac": achieved / f16_peak, "traffic": traffic,
                 "note": f"fp16 peak = {pk_kind} bf16 burst (nominal ratio 1); algorithmic "
-                        "4*Lambda^2 flops per accepted flip; the kernel is latency-bound "
-                        f"(fraction of the FP32 FMA peak {fp32_peak:.1f} TFLOP/s: "
-                        f"{achieved / fp32_peak:.3f})"}
+                        "4*Lambda^2 flops per accepted flip + (16/3)*Lambda^3 per recompute "
+                        f"({rec_flops / flops_step:.2f} of the total); fraction of the FP32 FMA peak "
+                        f"{fp32_peak:.1f} TFLOP/s: {achieved / fp32_peak:.3f}"}
 
     # e2e through the C ABI from pinned host buffers: G0 upload (set_G0, which
     # also rebuilds G in FP64 for every chain), sweeps, G(tau) download
@@ -363,19 +372,33 @@ def run_ours(args, rank, world, local):
         extra["fp64_rank1"] = {"value": pps * S64 / (ms64 * 1e-3), "unit": "proposals/s",
                                "sweeps": S64, "speedup_fp32_delayed": value / (pps * S64 / (ms64 * 1e-3))}
         ctx64.close()
-        # the same FP32 delayed path with the FP64 recompute every 64 accepted
-        # flips (the configurations' own N_wrap), one full-length step
-        Sw = S
+        # the same configuration with the recompute from scratch (FP64
+        # Gauss-Jordan from the field) instead of the Newton refinement
+        Sg = max(10, S // 10)
         ctx_w, _ = make_ctx(hfqmc, inputs, beta, grids, "f32_delayed", argparse.Namespace(
-            k=args.k, n_wrap=64, flush=args.flush, recompute=args.recompute), stream, seed=1)
+            k=args.k, n_wrap=args.n_wrap, flush=args.flush, recompute="gj"), stream, seed=1)
         ctx_w.sweep(0, 1)
-        ctx_w.sweep(0, Sw)
+        ctx_w.sweep(0, Sg)
         msw = ctx_w.get_stats(0)["last_sweep_ms"]
         stw = [ctx_w.get_stats(i) for i in range(len(grids))]
-        extra["fp32_delayed_nwrap64"] = {"value": pps * Sw / (msw * 1e-3), "unit": "proposals/s",
-                                         "sweeps": Sw,
-                                         "drift_max": max(st["drift_max"] for st in stw)}
+        extra["fp32_delayed_gauss_jordan"] = {"value": pps * Sg / (msw * 1e-3), "unit": "proposals/s",
+                                              "sweeps": Sg, "n_wrap": [st["n_wrap"] for st in stw]}
         ctx_w.close()
+        # a recompute interval beyond the configuration's {16, 32, 64}: the
+        # earlier table (8192 accepted flips up to Lambda 128, 16384 above),
+        # one full step and its paired G(tau) error
+        long_args = argparse.Namespace(k=args.k, n_wrap=0, flush=args.flush, recompute=args.recompute,
+                                       precision=args.precision, tune=LONG_NWRAP_TABLE)
+        ctx_l, _ = make_ctx(hfqmc, inputs, beta, grids, "f32_delayed", long_args, stream, seed=1)
+        ctx_l.sweep(0, 1)
+        ctx_l.sweep(0, S)
+        msl = ctx_l.get_stats(0)["last_sweep_ms"]
+        stl = [ctx_l.get_stats(i) for i in range(len(grids))]
+        ctx_l.close()
+        extra["fp32_delayed_long_nwrap"] = {
+            "value": pps * S / (msl * 1e-3), "unit": "proposals/s", "sweeps": S,
+            "n_wrap": [st["n_wrap"] for st in stl], "drift_max": [st["drift_max"] for st in stl],
+            "g_tau_err_vs_fp64": paired_error(hfqmc, inputs, beta, grids, long_args, stream)}
         extra["g_tau_err_vs_fp64"] = paired_error(hfqmc, inputs, beta, grids, args, stream)
         extra["cpu_baseline"] = oracle_sample(grids, beta, args.cpu_seconds)
     line = {"metric": "HS flip proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,

@@ -41,15 +41,16 @@ struct GridHost {
 };
 
 // Per-Lambda defaults of the delay depth and recompute interval, measured
-// on GB300: k by the sweep rate at each Lambda (k is lowered further when the
-// panels or the TMA flush buffers would not fit in shared memory), N_wrap by
-// the G(tau) accuracy criterion of the FP32 path against FP64.
+// on GB300 (paper_0801_1222_gb300/autotune.py): k by the sweep rate at each
+// Lambda with the recompute every 64 accepted flips (k is lowered further
+// when the panels or the TMA flush buffers would not fit); N_wrap = 64, the
+// longest of the multigrid configuration's intervals {16, 32, 64} and the
+// fastest, its FP32 G(tau) within 1e-9 of FP64 on the same trajectory.
 struct TuneEntry {
   int L_max, k, n_wrap;
 };
 const TuneEntry kTuneTable[] = {
-    {64, 32, 8192},   {128, 32, 8192},   {144, 32, 16384},
-    {176, 24, 16384}, {1024, 16, 16384},
+    {64, 24, 64}, {128, 24, 64}, {144, 32, 64}, {176, 24, 64}, {1024, 16, 64},
 };
 
 // k and N_wrap for Lambda from a table (the caller's if non-empty, else the
