@@ -423,11 +423,94 @@ def run_ours(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def run_dmft(args, rank, world, local):
+    """The multigrid DMFT workload (four U values x six grids, 1024 chains):
+    one step = one DMFT iteration of the batched loop -- every bath sampled on
+    its grids (hfqmc_set_G0, which also rebuilds every chain's G in FP64), one
+    hfqmc_sweep over all chains (200 unmeasured + --sweeps measured sweeps;
+    1000 unmeasured in the first warm-up iteration), and the host glue
+    (multigrid estimate, Fourier transform, Bethe update) per U.  value: the
+    sweeps' proposals over their device time; e2e: over the whole iteration."""
+    import torch
+
+    from paper_0801_1222_gb300 import dmft, hfqmc, inputs
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w, grids = workload(args.workload)
+    beta = w["beta"]
+    stream = torch.cuda.Stream()
+    ctx = hfqmc.HFQMC(beta, [g[0] for g in grids], [g[1] for g in grids], [g[3] for g in grids],
+                      seed=1 + rank, precision=args.precision, k=args.k, n_wrap=args.n_wrap, flush=args.flush,
+                      drift_fail=1.0, stream=stream, recompute=args.recompute)
+    loop = dmft.BatchedMultigridDMFT(ctx, beta, w["U"], [beta / L for L in w["L"]], n_fine=1001, n_iw=4096)
+    pps = proposals_per_sweep(grids)
+    first, later = w["sweeps"][0], w["sweeps_later"][0]
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for it in range(args.warmup):
+        loop.iterate(first if it == 0 else later, args.sweeps)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sweep_ms, iter_s = [], []
+    with Clocks(local) as clk:
+        for it in range(args.steps):
+            flush_buf.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for lp in loop.loops:
+                lp.set_baths()
+            ctx.sweep(later, args.sweeps)
+            sweep_ms.append(ctx.get_stats(0)["last_sweep_ms"])
+            recs = [lp.collect() for lp in loop.loops]
+            iter_s.append(time.perf_counter() - t0)
+    S = later + args.sweeps
+    value, total_ms = aggregate(sum(sweep_ms), pps * S * args.steps)
+    stats = [ctx.get_stats(i) for i in range(len(grids))]
+    extra = {}
+    if rank == 0 and not args.no_baselines:
+        ctx64 = hfqmc.HFQMC(beta, [g[0] for g in grids], [g[1] for g in grids], [g[3] for g in grids], seed=1,
+                            precision="f64_rank1", drift_fail=1.0, stream=stream)
+        for lp in loop.loops:  # the FP32 loop's current baths
+            for i, L in enumerate(lp.Ls):
+                ctx64.set_G0(lp.grid0 + i, lp.bath_on_grid(L))
+        S64 = max(2, args.sweeps // 100)
+        ctx64.sweep(0, 1)
+        ctx64.sweep(0, S64)
+        r64 = pps * S64 / (ctx64.get_stats(0)["last_sweep_ms"] * 1e-3)
+        extra["fp64_rank1"] = {"value": r64, "unit": "proposals/s", "sweeps": S64, "speedup_fp32_delayed": value / r64}
+        ctx64.close()
+    line = {"metric": "HS flip proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (Bethe W=4 bath, half filling; DMFT-updated baths)",
+            "config": {"workload": args.workload, "beta": beta, "U": w["U"], "grids_L": w["L"],
+                       "chains": sum(g[3] for g in grids), "sweeps_per_step": [later, args.sweeps],
+                       "precision": args.precision, "k": [st["k"] for st in stats[:len(w["L"])]],
+                       "n_wrap": [st["n_wrap"] for st in stats[:len(w["L"])]],
+                       "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * pps * S * args.steps / sum(iter_s), "unit": "proposals/s",
+                    "h2d_bytes_per_step": int(sum(8 * g[2] for g in grids)),
+                    "d2h_bytes_per_step": int(sum(16 * (g[2] + 1) + 16 for g in grids)),
+                    "s_per_iteration": sum(iter_s) / args.steps},
+            "gpu_launches": (3 + 4 * len(grids)) * args.steps, "clocks": clk.summary(),
+            "D": [r["D"] for r in recs], "D_err": [r["D_err"] for r in recs],
+            "accept_rate": [round(st["accept_rate"], 4) for st in stats], **extra}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "dmft_c5":
+        run_dmft(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

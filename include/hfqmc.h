@@ -74,7 +74,10 @@ typedef void (*hfqmc_free_fn)(void *ptr, void *user);
 typedef struct {
     int precision;      /* HFQMC_F64_RANK1 | HFQMC_F32_RANK1 | HFQMC_F32_DELAYED    */
     int k;              /* delay depth for F32_DELAYED (8..64, multiple of 8); 0 = per-Lambda table */
-    int n_wrap;         /* FP64 recompute every n_wrap accepted flips; 0 = per-Lambda table; <0 = never */
+    int n_wrap;         /* FP64 recompute every n_wrap accepted flips; <0 = never; 0 = per-Lambda table
+                           (F32_DELAYED: 64, the multigrid configuration's interval; rank-1 paths
+                           without a tune_table: 16384 for F64_RANK1, 8192 / 16384 (Lambda > 128)
+                           for F32_RANK1) */
     int accept_rule;    /* HFQMC_METROPOLIS (accept iff u < R) | HFQMC_HEAT_BATH (u (1+R) < R) */
     double drift_warn;  /* recorded only */
     double drift_fail;  /* hfqmc_sweep returns HFQMC_EDRIFT above this (<= 0: never; default 1e-1) */
@@ -139,10 +142,11 @@ typedef struct hfqmc_ctx hfqmc_ctx;
 
 /* Fills *opts with defaults: F32_DELAYED, k = 0, n_wrap = 0 (table), Metropolis,
  * drift_warn 1e-6, drift_fail 1e-1, own stream, autotune on, flush auto,
- * graphs on, no allocator hooks.  drift_fail guards against a broken chain:
- * at the table's N_wrap the FP32 matrix drift max|G_fast - G_fresh| reaches
- * a few 1e-2 (maximum over chains) while G(tau) stays within its 1e-5
- * criterion, so the default sits an order of magnitude above that. */
+ * graphs on, no allocator hooks, recompute auto (Newton refinement on the
+ * delayed path).  drift_fail guards against a broken chain: at the table's
+ * N_wrap = 64 the FP32 matrix drift max|G_fast - G_fresh| stays below 1e-2
+ * (maximum over chains; a few 1e-2 at intervals of 8192 or more) while G(tau)
+ * stays within its 1e-5 criterion, so the default sits above that. */
 void hfqmc_default_opts(hfqmc_opts *opts);
 
 /* Creates a context for one beta and one U over n_grids dtau grids.

@@ -77,7 +77,7 @@ __host__ __device__ inline size_t del_stage_bytes(int K, int L, int ub) {
 }
 
 __host__ __device__ inline size_t rf_smem_need(int L) {
-  // rf_smem_bytes of hfq_refine.cuh: the larger of GEMM1's K chunk (A and H'
+  // the Newton refinement (hfq_refine.cuh): the larger of its two stage buffers of the residual product (A and H'
   // slices) and GEMM2's (H' and E^T hi / lo parts)
   const size_t g2 = (size_t)2 * 128 * kRf2KC * 2 + (size_t)2 * ((L + 15) / 16 * 16) * kRf2KC * 2;
   return g2 > (size_t)kRfSmem ? g2 : (size_t)kRfSmem;

@@ -41,12 +41,12 @@ constexpr int kRfBits = 7;        // bits per slice
 constexpr int kRfSlicesA = 6;     // slices of A (42 bits)
 constexpr int kRfSlicesH = 4;     // slices of H' (28 bits)
 constexpr int kRfLevels = 6;      // products p + q = 0 .. 5 kept, one FP32 accumulator per level
-constexpr int kRfN = 64;          // columns of G per product tile
+constexpr int kRfNMax = 80;       // columns of G per product tile: 64 or 80 per grid (rc.nN)
 constexpr int kRfKC = 32;         // K (contraction) extent of one staged chunk of the residual product
 constexpr int kRf2KC = 64;        // the same for the update product
 constexpr int kRfTileA = 128 * kRfKC * 2;        // bytes of one A slice of a (row block, K chunk)
-constexpr int kRfTileH = kRfN * kRfKC * 2;       // bytes of one H' slice of a (column block, K chunk)
-constexpr int kRfStage = kRfSlicesA * kRfTileA + kRfSlicesH * kRfTileH;  // 64 KiB: one chunk
+constexpr int kRfTileH = kRfNMax * kRfKC * 2;    // bytes of one H' slice of a (column block, K chunk)
+constexpr int kRfStage = kRfSlicesA * kRfTileA + kRfSlicesH * kRfTileH;  // 68 KiB: one chunk
 constexpr int kRfSmem = 2 * kRfStage;            // two stage buffers
 
 struct RefineConst {
@@ -55,6 +55,7 @@ struct RefineConst {
   int ea;                // |A| < 2^ea (the slices' common scale)
   int nrb, nkc;          // row blocks of 128, K chunks of 64 (Lambda padded)
   float emax_step;       // Newton steps only while max |E| <= emax_step (else from scratch)
+  int nN;                // columns of G per product tile: 64 or 80, whichever pads Lambda less
   float cplus[2];        // e^{+lambda}, e^{-lambda} in FP32: (1 + d_j) for sigma s_j = +1, -1
   float cminus_hi[2];    // e^{-sigma lambda s_j} = 1 / (1 + d_j) as an FP32 pair (hi + lo)
   float cminus_lo[2];

@@ -54,8 +54,8 @@ static_assert(kDelNT == 512, "the refinement's TMEM read-out assumes 16 warps");
 // of the last warp, which cuts no H' slices, so the issue overlaps the
 // slicing of the next chunk (threads 0 .. 255).
 constexpr int kRfIssuer = kDelNT - 32;
-static_assert(kRfIssuer >= kRfN * (kRfKC / 8), "the MMA issuer must not slice");
-static_assert(kTmemCols >= kRfLevels * kRfN, "level accumulators must fit the TMEM allocation");
+static_assert(kRfIssuer >= kRfNMax * (kRfKC / 8), "the MMA issuer must not slice");
+static_assert(kTmemCols >= kRfLevels * kRfNMax, "level accumulators must fit the TMEM allocation");
 
 // K-major core-matrix layout (8 rows x 16 bytes per core matrix, contiguous
 // along K): element (r, m) of a tile with K extent kRfKC (the residual
@@ -129,9 +129,9 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
   const int L = gc.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kDelNT / 32;
-  const int q4 = warp & 3, g4 = warp >> 2;  // TMEM lane quarter, column group
+  const int q4 = warp & 3, g4 = warp >> 2;  // TMEM lane quarter, column group (the update's epilogue)
   const int nkc = rc.nkc, nrb = rc.nrb;
-  const int nnb = rf_pad(L, kRfN) / kRfN;
+  const int nN = rc.nN, nnb = rf_pad(L, nN) / nN;
   float* wsE = ws;
   const uint32_t sm0 = smem_u32(sm);
   // the row factors in registers: (1 + d_j) and its inverse as an FP32 pair,
@@ -178,7 +178,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
     // Every commit of a chunk's MMAs is waited for exactly once, in order,
     // so each barrier's parity stays in step.
     float emax = 0.f;
-    const uint32_t idesc1 = make_idesc_f16(kRfN);
+    const uint32_t idesc1 = make_idesc_f16(nN);
     bool bad = false;  // a bounded wait gave up
     auto stage_in = [&](int nb, int rb, int kc, int b) {
       const uint32_t bar = tc->cbar + 8u * (uint32_t)b;
@@ -187,9 +187,10 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
         bulk_g2s(sm0 + (uint32_t)(b * kRfStage), rc.aslc + (size_t)(rb * nkc + kc) * kRfSlicesA * (kRfTileA / 2),
                  (uint32_t)(kRfSlicesA * kRfTileA), bar);
       }
-      if (tid < kRfN * (kRfKC / 8)) {
+      if (tid < nN * (kRfKC / 8)) {
         // a column and eight rows of H' per thread, sliced into the buffer
-        const int n = nb * kRfN + (tid & (kRfN - 1)), j0 = kc * kRfKC + (tid >> 6) * 8;
+        const int j8 = tid / nN, nl = tid - j8 * nN;
+        const int n = nb * nN + nl, j0 = kc * kRfKC + j8 * 8;
         float y[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -201,7 +202,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
           const int j = j0 + t;
           y[t] = y[t] * (j < L && sig * s[j] > 0 ? cpl0 : cpl1) * s7;
         }
-        unsigned char* dst = sm + b * kRfStage + kRfSlicesA * kRfTileA + rf_off(n & (kRfN - 1), j0 & (kRfKC - 1));
+        unsigned char* dst = sm + b * kRfStage + kRfSlicesA * kRfTileA + rf_off(nl, j8 * 8);
 #pragma unroll
         for (int q = 0; q < kRfSlicesH; ++q) {
           // slice q: rint of the running remainder, which moves up 7 bits
@@ -268,7 +269,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
                   if (lv >= kRfLevels) continue;
                   const int first_p = lv > kRfSlicesH - 1 ? lv - (kRfSlicesH - 1) : 0;
                   const int acc = (kc > 0 || kk > 0 || p != first_p) ? 1 : 0;
-                  tc_mma_f16(tc->tmem + (uint32_t)(lv * kRfN), da + (uint64_t)(p * (kRfTileA >> 4)),
+                  tc_mma_f16(tc->tmem + (uint32_t)(lv * nN), da + (uint64_t)(p * (kRfTileA >> 4)),
                              db + (uint64_t)(q * (kRfTileH >> 4)), idesc1, acc);
                 }
             }
@@ -285,36 +286,41 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
           return -1.f;
         }
         tc_fence_after();
-        // the six level sums of this thread's row and 16 columns (8 at a
-        // time), combined in 64-bit integers, then E = delta - V 2^{ea+eh-49}
-        const int i = rb * 128 + 32 * q4 + lane;
+        // the six level sums of a row and 16 columns per task (TMEM lane
+        // quarter warp % 4, columns 16 g ..), 8 at a time, combined in 64-bit
+        // integers, then E = delta - V 2^{ea+eh-49}
         const long long one = 1ll << sh;
 #pragma unroll 1
-        for (int h8 = 0; h8 < 2; ++h8) {
-          long long V[8];
+        for (int task = warp; task < 4 * (nN / 16); task += NW) {
+          const int g16 = task >> 2;
+          const int i = rb * 128 + 32 * q4 + lane;
+#pragma unroll 1
+          for (int h8 = 0; h8 < 2; ++h8) {
+            long long V[8];
 #pragma unroll
-          for (int c = 0; c < 8; ++c) V[c] = 0;
+            for (int c = 0; c < 8; ++c) V[c] = 0;
 #pragma unroll
-          for (int lv = 0; lv < kRfLevels; ++lv) {
-            float v[8];
-            tmem_ld8(tc->tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(lv * kRfN + 16 * g4 + 8 * h8), v);
+            for (int lv = 0; lv < kRfLevels; ++lv) {
+              float v[8];
+              tmem_ld8(tc->tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(lv * nN + 16 * g16 + 8 * h8), v);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) V[c] = V[c] * (1ll << kRfBits) + (long long)__float2int_rn(v[c]);
-          }
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int n = nb * kRfN + 16 * g4 + 8 * h8 + c;
-            const long long Ei = (i == n ? one : 0ll) - V[c];
-            float E;
-            if (Ei > (1ll << 54) || Ei < -(1ll << 54)) {
-              E = __int_as_float(0x7f800000);  // far beyond the step's range
-            } else {
-              const float hi = (float)(int)(Ei >> 24), lo = (float)(int)(Ei & 0xffffffll);
-              E = fmaf(hi, 16777216.f, lo) * pow2f(-sh);
+              for (int c = 0; c < 8; ++c) V[c] = V[c] * (1ll << kRfBits) + (long long)__float2int_rn(v[c]);
             }
-            if (i < L && n < L) {
-              wsE[(size_t)n * L + i] = E;  // E^T: lanes (rows i) write consecutive words
-              emax = fmaxf(emax, fabsf(E));
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const int n = nb * nN + 16 * g16 + 8 * h8 + c;
+              const long long Ei = (i == n ? one : 0ll) - V[c];
+              float E;
+              if (Ei > (1ll << 54) || Ei < -(1ll << 54)) {
+                E = __int_as_float(0x7f800000);  // far beyond the step's range
+              } else {
+                const float hi = (float)(int)(Ei >> 24), lo = (float)(int)(Ei & 0xffffffll);
+                E = fmaf(hi, 16777216.f, lo) * pow2f(-sh);
+              }
+              if (i < L && n < L) {
+                wsE[(size_t)n * L + i] = E;  // E^T: lanes (rows i) write consecutive words
+                emax = fmaxf(emax, fabsf(E));
+              }
             }
           }
         }

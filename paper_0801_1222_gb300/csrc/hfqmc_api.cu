@@ -348,7 +348,14 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   for (int g = 0; g < n_grids; ++g) {
     GridHost& h = c->gh[g];
     int k_t = 16, nw_t = 1024;
-    if (o.autotune) tune_lookup(h.L, user_table, &k_t, &nw_t);
+    if (o.autotune) {
+      tune_lookup(h.L, user_table, &k_t, &nw_t);
+      // the built-in table is the delayed path's; the rank-1 paths recompute
+      // from scratch at a long interval (FP64: the drift of 16384 flips is
+      // ~1e-12; FP32 rank-1: the interval validated for its G(tau))
+      if (o.precision != HFQMC_F32_DELAYED && user_table.empty())
+        nw_t = (o.precision == HFQMC_F64_RANK1 || h.L > 128) ? 16384 : 8192;
+    }
     h.k = (o.precision == HFQMC_F32_DELAYED) ? (o.k ? o.k : k_t) : 1;
     h.n_wrap = o.n_wrap ? o.n_wrap : nw_t;
     size_t sm;
@@ -514,6 +521,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
       r.nrb = (L + 127) / 128;
       r.nkc = (L + kRfKC - 1) / kRfKC;
       r.emax_step = o.refine_max == 0.0 ? 0.00390625f : (o.refine_max < 0.0 ? -1.f : (float)o.refine_max);
+      r.nN = (L + 79) / 80 * 80 < (L + 63) / 64 * 64 ? 80 : 64;
       r.cplus[0] = (float)std::exp(lam);
       r.cplus[1] = (float)std::exp(-lam);
       for (int v = 0; v < 2; ++v) {

@@ -78,9 +78,11 @@ def extrapolate_scalar(dtaus, values, errors=None):
 
 class MultigridDMFT:
     """Multigrid HF-QMC DMFT on the Bethe lattice.  ``solver`` is an
-    ``hfqmc.HFQMC`` context over the grids ``dtaus`` (one U)."""
+    ``hfqmc.HFQMC`` context (or anything with its set_G0 / sweep / get_G /
+    get_D calls, e.g. the oracle) over the grids ``dtaus`` of one U, starting
+    at grid index ``grid0`` of the solver."""
 
-    def __init__(self, solver, beta, dtaus, n_fine=1001, n_iw=4096, mix=1.0):
+    def __init__(self, solver, beta, dtaus, n_fine=1001, n_iw=4096, mix=1.0, grid0=0):
         self.solver = solver
         self.beta = float(beta)
         self.dtaus = list(dtaus)
@@ -88,18 +90,29 @@ class MultigridDMFT:
         self.tau_fine = np.linspace(0.0, self.beta, n_fine)
         self.n_iw = n_iw
         self.mix = mix
+        self.grid0 = int(grid0)
         self.G0_iw = inputs.bethe_G0_iw(1j * matsubara(self.beta, n_iw))
         self.history = []
 
     def bath_on_grid(self, L):
         return bath_tau(self.beta, np.arange(L) * self.beta / L, self.G0_iw)
 
-    def iterate(self, n_warm, n_meas):
+    def set_baths(self):
+        """The current bath, sampled on every grid of this loop."""
         for i, L in enumerate(self.Ls):
-            self.solver.set_G0(i, self.bath_on_grid(L))
+            self.solver.set_G0(self.grid0 + i, self.bath_on_grid(L))
+
+    def iterate(self, n_warm, n_meas):
+        self.set_baths()
         self.solver.sweep(n_warm, n_meas)
-        Gs, Es = zip(*[self.solver.get_G(i) for i in range(len(self.Ls))])
-        Ds = [self.solver.get_D(i) for i in range(len(self.Ls))]
+        return self.collect()
+
+    def collect(self):
+        """After the sweeps: the multigrid estimate, its transform and the
+        Bethe update of the bath."""
+        idx = [self.grid0 + i for i in range(len(self.Ls))]
+        Gs, Es = zip(*[self.solver.get_G(i) for i in idx])
+        Ds = [self.solver.get_D(i) for i in idx]
         ref = lambda t: bath_tau(self.beta, t, self.G0_iw)
         G_fine, G_err, _ = mg.multigrid_estimate(self.beta, self.dtaus, list(Gs), list(Es),
                                                  self.tau_fine, ref)
@@ -110,6 +123,26 @@ class MultigridDMFT:
         rec = dict(G_fine=G_fine, G_err=G_err, G_iw=G_iw, D_grids=[d[0] for d in Ds], D=D, D_err=D_err)
         self.history.append(rec)
         return rec
+
+
+class BatchedMultigridDMFT:
+    """Several independent multigrid DMFT loops -- one per interaction U --
+    whose impurity problems share one solver context (grid index u * n_dtau +
+    i for U[u] and dtau[i], created with a per-grid U): every iteration sets
+    all baths, runs one sweep call over every chain of every (U, dtau) grid,
+    then updates each U's bath from its own grids."""
+
+    def __init__(self, solver, beta, Us, dtaus, n_fine=1001, n_iw=4096, mix=1.0):
+        self.solver = solver
+        self.Us = list(Us)
+        self.loops = [MultigridDMFT(solver, beta, dtaus, n_fine=n_fine, n_iw=n_iw, mix=mix,
+                                    grid0=u * len(dtaus)) for u in range(len(self.Us))]
+
+    def iterate(self, n_warm, n_meas):
+        for lp in self.loops:
+            lp.set_baths()
+        self.solver.sweep(n_warm, n_meas)
+        return [lp.collect() for lp in self.loops]
 
 
 class FixedDtauDMFT(MultigridDMFT):

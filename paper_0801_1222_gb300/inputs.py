@@ -86,6 +86,12 @@ WORKLOADS = {
                                chains=[64] * 6, sweeps=(1_000, 10_000), precision="f32_delayed"),
     "large_L500": dict(U=[4.8], beta=50.0, L=[500], chains=[128], sweeps=(1_000, 10_000),
                        precision="f32_delayed", k=64, n_wrap=64),
+    # the multigrid DMFT loop: four U values x six grids, 1024 chains (42 per
+    # (U, dtau) pair, the 16 left over on the largest Lambda), 15 iterations;
+    # sweeps (warm-up, measured) of the first and of the later iterations
+    "dmft_c5": dict(U=[4.6, 4.8, 5.0, 5.2], beta=40.0, L=[80, 120, 160, 200, 240, 320],
+                    chains=[42, 42, 42, 42, 42, 46], sweeps=(1_000, 10_000), sweeps_later=(200, 10_000),
+                    iterations=15, precision="f32_delayed"),
 }
 
 
