@@ -117,6 +117,10 @@ typedef struct {
     double refine_max;  /* REFINE: the largest max |1 - G^{-1} G| for which Newton steps are taken
                            (0 = the default 2^-8; < 0 = never, every recompute from scratch);
                            above 2^-13 a second step follows */
+    int ph_symmetry;    /* F32_DELAYED, REFINE: 0 = when hfqmc_set_G0 finds the bath particle-hole
+                           symmetric (G0(tau_k) = G0(beta - tau_k), G0(0+) = -1/2, to 1e-12: half
+                           filling), a recompute refines G_up and sets G_dn = 1 - G_up^T, an identity
+                           every field configuration satisfies then; < 0 = never */
 } hfqmc_opts;
 
 enum { HFQMC_RECOMPUTE_AUTO = 0, HFQMC_RECOMPUTE_GJ = 1, HFQMC_RECOMPUTE_REFINE = 2 };
@@ -136,6 +140,7 @@ typedef struct {
     double drift_max;       /* max |G_fast - G_fresh| over recomputes since set_G0 */
     double last_sweep_ms;   /* device time of the last hfqmc_sweep (whole batch) */
     int64_t recompute_fallbacks; /* recomputes the Newton refinement handed to Gauss-Jordan */
+    int ph_symmetric;       /* 1: the grid's bath is particle-hole symmetric (see opts.ph_symmetry) */
 } hfqmc_stats;
 
 typedef struct hfqmc_ctx hfqmc_ctx;

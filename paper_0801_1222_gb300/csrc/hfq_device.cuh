@@ -89,6 +89,9 @@ struct GridConst {
   const void* tmapG;  // TMA tensor map (CUtensorMap, global memory) over the FP32 G of
                       // all chains: dims {column, row, spin, chain}; null unless gtile
   const RefineConst* rc;  // recompute by Newton refinement (FP32 delayed path); null: Gauss-Jordan
+  int ph;                 // the bath is particle-hole symmetric (M + M^T = 1): every field has
+                          // G_dn = 1 - G_up^T, so a recompute rebuilds G_up and mirrors it
+  int pad2;
 };
 
 struct ChainCounters {

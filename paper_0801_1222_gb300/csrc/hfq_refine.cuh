@@ -454,4 +454,39 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
   return rf_block_max(drift, red);
 }
 
+// G_dn = 1 - G_up^T for a particle-hole symmetric bath (both L x L FP32 in
+// global memory), through per-warp 32 x 33 shared-memory tiles (tile: 16
+// warps x 32 x 33 floats) so that reads and writes are both coalesced.
+// Returns max |G_dn(old) - G_dn(new)| (block-wide).  All threads call it.
+__device__ inline float ph_mirror(const float* Gu, float* Gd, int L, float* tile, float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kDelNT / 32;
+  float* tw = tile + warp * 32 * 33;
+  const int nt = (L + 31) / 32;
+  float drift = 0.f;
+  for (int t = warp; t < nt * nt; t += NW) {
+    const int ti = t / nt, tj = t - ti * nt;  // source tile rows ti*32.., columns tj*32..
+    const int c = tj * 32 + lane;
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const int i = ti * 32 + r;
+      tw[r * 33 + lane] = (i < L && c < L) ? Gu[(size_t)i * L + c] : 0.f;
+    }
+    __syncwarp();
+    const int cc = ti * 32 + lane;  // destination column = source row
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const int i = tj * 32 + r;      // destination row = source column
+      if (i < L && cc < L) {
+        const float gn = (i == cc ? 1.f : 0.f) - tw[lane * 33 + r];
+        const size_t o = (size_t)i * L + cc;
+        drift = fmaxf(drift, fabsf(Gd[o] - gn));
+        Gd[o] = gn;
+      }
+    }
+    __syncwarp();
+  }
+  return rf_block_max(drift, red);
+}
+
 }  // namespace hfq

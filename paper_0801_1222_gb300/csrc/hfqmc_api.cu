@@ -429,6 +429,9 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     q.M = nullptr;
     q.Minv = nullptr;
     q.tmapG = nullptr;
+    q.rc = nullptr;
+    q.ph = 0;
+    q.pad2 = 0;
   }
 
   // device memory: one pool, grid-major per category
@@ -669,6 +672,20 @@ int hfqmc_set_G0(hfqmc_ctx* c, int grid, const double* G0_tau) {
   GridHost& h = c->gh[grid];
   for (int k = 0; k < h.L; ++k)
     if (!std::isfinite(G0_tau[k])) return fail(c, HFQMC_EINVAL, "G0_tau holds a non-finite value");
+  // particle-hole symmetric bath (M + M^T = 1): G0(tau_k) = G0(beta - tau_k) and
+  // G0(0+) = -1/2, to 1e-12 (a Matsubara sum gives ~1e-13; the mirrored G_dn
+  // then differs from the exact one by ~1e-12 x the condition of G^{-1},
+  // far below FP32 rounding)
+  int ph = 0;
+  if (c->opts.ph_symmetry >= 0 && c->opts.precision == HFQMC_F32_DELAYED) {
+    double dev = std::fabs(G0_tau[0] + 0.5);
+    for (int k = 1; k < h.L; ++k) dev = std::max(dev, std::fabs(G0_tau[k] - G0_tau[h.L - k]));
+    ph = dev <= 1e-12;
+  }
+  if (ph != c->gc[grid].ph) {
+    c->gc[grid].ph = ph;
+    CK(cudaMemcpyAsync(c->d_grids + grid, &c->gc[grid], sizeof(GridConst), cudaMemcpyHostToDevice, c->stream));
+  }
   double* dM = const_cast<double*>(c->gc[grid].M);
   double* dG0 = (double*)((unsigned char*)dM + align256(sizeof(double) * (size_t)h.L * h.L));
   CK(cudaMemcpyAsync(dG0, G0_tau, sizeof(double) * h.L, cudaMemcpyHostToDevice, c->stream));
@@ -806,6 +823,7 @@ int hfqmc_get_stats(hfqmc_ctx* c, int grid, hfqmc_stats* out) {
   out->drift_max = o.drift;
   out->last_sweep_ms = c->last_ms;
   out->recompute_fallbacks = o.fallbacks;
+  out->ph_symmetric = c->gc[grid].ph;
   return HFQMC_OK;
 }
 

@@ -324,9 +324,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             float* rws = reinterpret_cast<float*>(ip.ws);
             float* rred = reinterpret_cast<float*>(red);
             const float d0 = refine_spin(gc, *gc.rc, ss, 1, Ggl, rws, smem + lay.off_rf, &tc, rred, a.status, &steps);
-            const float d1 = d0 >= 0.f ? refine_spin(gc, *gc.rc, ss, -1, Ggl + (size_t)L * L, rws, smem + lay.off_rf,
-                                                     &tc, rred, a.status, &steps)
-                                       : -1.f;
+            // spin down: mirrored for a particle-hole symmetric bath, else refined too
+            const float d1 = d0 < 0.f ? -1.f
+                             : gc.ph ? ph_mirror(Ggl, Ggl + (size_t)L * L, L,
+                                                 reinterpret_cast<float*>(smem + lay.off_rf), rred)
+                                     : refine_spin(gc, *gc.rc, ss, -1, Ggl + (size_t)L * L, rws, smem + lay.off_rf,
+                                                   &tc, rred, a.status, &steps);
             if (d0 >= 0.f && d1 >= 0.f)
               d = fmax((double)d0, (double)d1);
             else

@@ -50,7 +50,7 @@ class hfqmc_opts(ctypes.Structure):
                 ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_user", ctypes.c_void_p),
                 ("resident_kb", ctypes.c_int), ("gj_smem", ctypes.c_int), ("gtile", ctypes.c_int),
                 ("tune_table", ctypes.POINTER(ctypes.c_int)), ("tune_entries", ctypes.c_int),
-                ("recompute", ctypes.c_int), ("refine_max", ctypes.c_double)]
+                ("recompute", ctypes.c_int), ("refine_max", ctypes.c_double), ("ph_symmetry", ctypes.c_int)]
 
 
 class hfqmc_stats(ctypes.Structure):
@@ -59,7 +59,8 @@ class hfqmc_stats(ctypes.Structure):
                 ("proposals", ctypes.c_int64), ("accepted", ctypes.c_int64),
                 ("recomputes", ctypes.c_int64), ("numeric_errors", ctypes.c_int64),
                 ("accept_rate", ctypes.c_double), ("drift_max", ctypes.c_double),
-                ("last_sweep_ms", ctypes.c_double), ("recompute_fallbacks", ctypes.c_int64)]
+                ("last_sweep_ms", ctypes.c_double), ("recompute_fallbacks", ctypes.c_int64),
+                ("ph_symmetric", ctypes.c_int)]
 
 
 _lib = None
@@ -277,7 +278,7 @@ class HFQMC:
     def __init__(self, beta, U, dtau, chains_per_grid, seed=1, precision="f32_delayed", k=0,
                  n_wrap=0, accept_rule="metropolis", drift_fail=1e-1, flush="auto",
                  use_graph=True, stream=None, torch_alloc=True, resident_kb=0, gj_smem=0,
-                 gtile=0, tune=None, autotune=True, recompute="auto", refine_max=0.0):
+                 gtile=0, tune=None, autotune=True, recompute="auto", refine_max=0.0, ph_symmetry=0):
         o = hfqmc_default_opts()
         o.precision = PRECISION[precision]
         o.k = int(k)
@@ -292,6 +293,7 @@ class HFQMC:
         o.autotune = 1 if autotune else 0
         o.recompute = RECOMPUTE[recompute]
         o.refine_max = float(refine_max)
+        o.ph_symmetry = int(ph_symmetry)
         if tune is not None:  # [(Lambda_max, k, n_wrap), ...] (see autotune.py)
             flat = [int(v) for e in tune for v in e]
             self._tune = (ctypes.c_int * len(flat))(*flat)

@@ -115,3 +115,32 @@ def test_paired_G_tau_with_refine_at_nwrap_64():
         assert r["stats"]["recompute_fallbacks"] == 0
         assert np.max(np.abs(r["mean"])) < 1e-7
         _assert_within(r, 100)
+
+
+def test_particle_hole_mirror_and_both_spins_refined(orc):
+    """A particle-hole symmetric bath (the Bethe bath at half filling) turns
+    the mirror on: the recompute refines G_up and sets G_dn = 1 - G_up^T.  With
+    ph_symmetry = -1, or for a bath that is not symmetric, both spins are
+    refined.  Every variant leaves G_up and G_dn within 4x FP32 rounding of the
+    oracle's fresh FP64 inverses (n_wrap = 1)."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    beta, U, L = 20.0, 5.0, 200
+    sym = inputs.bethe_G0_tau(beta, L)
+    tau = np.arange(L) * beta / L
+    asym = sym + 2e-3 * np.sin(2 * np.pi * tau / beta)  # G0(tau) != G0(beta - tau)
+    for g0, phs, expect in ((sym, 0, 1), (sym, -1, 0), (asym, 0, 0)):
+        ctx = h.HFQMC(beta, U, [beta / L], [2], seed=4, precision="f32_delayed", n_wrap=1,
+                      drift_fail=1.0, recompute="refine", ph_symmetry=phs)
+        ctx.set_G0(0, g0)
+        ctx.sweep(0, 1)
+        st = ctx.get_stats(0)
+        assert st["ph_symmetric"] == expect and st["recompute_fallbacks"] == 0
+        M = orc.bath_matrix(g0)
+        lam = orc.lam(beta / L, U)
+        for c in range(2):
+            ch = ctx.get_chain(0, c)
+            for sig, G in ((1, ch["Gup"]), (-1, ch["Gdn"])):
+                Gx, _ = orc.green(M, ch["s"], lam, sig)
+                assert np.max(np.abs(G - Gx)) <= 4.0 * _fp32_rounding(Gx) + 1e-9, (phs, expect, c, sig)
+        ctx.close()
