@@ -64,11 +64,12 @@ struct RefineConst {
 
 __host__ __device__ inline int rf_pad(int L, int m) { return (L + m - 1) / m * m; }
 // Bytes of A's slice table of one grid, and of the per-chain workspace the
-// refinement needs (E in FP32; the chain's FP64 Gauss-Jordan workspace has room).
+// refinement needs (E^T in FP32, rows padded to a multiple of four floats;
+// the chain's FP64 Gauss-Jordan workspace has room).
 __host__ __device__ inline size_t rf_aslc_bytes(int L) {
   return (size_t)(rf_pad(L, 128) / 128) * (rf_pad(L, kRfKC) / kRfKC) * kRfSlicesA * kRfTileA;
 }
-__host__ __device__ inline size_t rf_ws_bytes(int L) { return (size_t)L * L * 4; }
+__host__ __device__ inline size_t rf_ws_bytes(int L) { return (size_t)L * rf_pad(L, 4) * 4; }
 
 struct GridConst {
   int L;           // Lambda

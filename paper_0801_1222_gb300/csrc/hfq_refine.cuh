@@ -111,13 +111,39 @@ __device__ __forceinline__ float rf_block_max(float v, float* red) {
   return r;
 }
 
+// x[0..7] = p[0..7], entries t >= n read as 0.  vec: p is 16-byte aligned
+// and n is a multiple of four (or <= 0), so two float4 loads serve.
+__device__ __forceinline__ void rf_ld8(const float* p, int n, bool vec, float* x) {
+  if (vec) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (n >= 4) a = *reinterpret_cast<const float4*>(p);
+    if (n >= 8) b = *reinterpret_cast<const float4*>(p + 4);
+    x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = t < n ? p[t] : 0.f;
+  }
+}
+
+// p[0..7] = x[0..7] for t < n (same vec contract as rf_ld8)
+__device__ __forceinline__ void rf_st8(float* p, int n, bool vec, const float* x) {
+  if (vec) {
+    if (n >= 4) *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    if (n >= 8) *reinterpret_cast<float4*>(p + 4) = make_float4(x[4], x[5], x[6], x[7]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t < n) p[t] = x[t];
+  }
+}
+
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
 }
 
 // One spin: G (L x L, row-major, FP32, in global memory) is replaced by its
 // Newton-refined value.  s: the field (shared memory); sig: +1 / -1; ws: the
-// chain's workspace (L x L floats for E); sm: rf_smem_need(L) of 1024-byte aligned
+// chain's workspace (E^T: L rows of rf_pad(L, 4) floats); sm: rf_smem_need(L) of 1024-byte aligned
 // shared memory; tc: the CTA's TMEM allocation and mbarriers (tc->cbar: bulk
 // copies into the two stage buffers, then their MMA completions).
 // Returns the largest change of an entry (>= 0), or -1 if the caller must
@@ -133,6 +159,8 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
   const int nkc = rc.nkc, nrb = rc.nrb;
   const int nN = rc.nN, nnb = rf_pad(L, nN) / nN;
   float* wsE = ws;
+  const int ldE = rf_pad(L, 4);     // row stride of E^T in ws
+  const bool vec = (L & 3) == 0;    // rows of G 16-byte aligned: float4 accesses
   const uint32_t sm0 = smem_u32(sm);
   // the row factors in registers: (1 + d_j) and its inverse as an FP32 pair,
   // selected by sigma s_j (index 0: +1, 1: -1)
@@ -317,10 +345,11 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
                 const float hi = (float)(int)(Ei >> 24), lo = (float)(int)(Ei & 0xffffffll);
                 E = fmaf(hi, 16777216.f, lo) * pow2f(-sh);
               }
-              if (i < L && n < L) {
-                wsE[(size_t)n * L + i] = E;  // E^T: lanes (rows i) write consecutive words
-                emax = fmaxf(emax, fabsf(E));
-              }
+              // E^T: lanes (rows i) write consecutive words; rows i >= L of E
+              // are exactly 0 (A's table is zero there), which fills the
+              // padding of E^T's rows
+              if (i < ldE && n < L) wsE[(size_t)n * ldE + i] = E;
+              if (i < L && n < L) emax = fmaxf(emax, fabsf(E));
             }
           }
         }
@@ -347,52 +376,70 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
     const float sE = pow2f(se), sHi = pow2f(eh - 28), sQ = pow2f(eh - 14 - se);
     for (int rb = 0; rb < nrb; ++rb) {
       for (int kc = 0; kc < nkc2; ++kc) {
-        // A: H' of rows rb*128.. (x 2^{14-eh}, below 2^14), hi / lo
+        // A: H' of rows rb*128.. (x 2^{14-eh}, below 2^14), hi / lo: 1024
+        // chunks of eight K values, two per thread, the loads of both first.
         // chunk c: row ((c >> 6) << 3) | (c & 7), K offset ((c >> 3) & 7) * 8, so
         // eight lanes write one 128-byte core-matrix row group (no bank conflict)
-        for (int c = tid; c < 128 * (kRf2KC / 8); c += kDelNT) {
-          const int r = ((c >> 6) << 3) | (c & 7), m0 = ((c >> 3) & 7) << 3;
-          const int i = rb * 128 + r;
-          const float cp = (i < L && sig * s[i] > 0) ? cpl0 : cpl1;
-          float x[8];
+        {
+          static_assert(128 * (kRf2KC / 8) == 2 * kDelNT, "two H' chunks per thread");
+          float x[2][8];
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {  // all loads first
-            const int k = kc * kRf2KC + m0 + t;
-            x[t] = (i < L && k < L) ? G[(size_t)i * L + k] : 0.f;
+          for (int u = 0; u < 2; ++u) {
+            const int c = tid + u * kDelNT;
+            const int i = rb * 128 + (((c >> 6) << 3) | (c & 7)), k0 = kc * kRf2KC + (((c >> 3) & 7) << 3);
+            rf_ld8(G + (size_t)(i < L ? i : 0) * L + k0, i < L ? L - k0 : 0, vec, x[u]);
           }
-          uint32_t h[4], l[4];
 #pragma unroll
-          for (int t = 0; t < 8; t += 2) {
-            const float xa = rintf(x[t] * cp * sH) * 0x1p-14f, xb = rintf(x[t + 1] * cp * sH) * 0x1p-14f;
-            h[t / 2] = f32x2_to_f16x2(xa, xb);
-            l[t / 2] = f32x2_to_f16x2(xa - f16_lo_to_f32(h[t / 2]), xb - f16_hi_to_f32(h[t / 2]));
-          }
-          const uint32_t off = rf_off2(r, m0);
-          *reinterpret_cast<uint4*>(sm + off) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(sm + 128 * kRf2KC * 2 + off) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-        // B: E^T (row n = column n of E, K = rows of E) x 2^se, hi / lo;
-        // wsE holds E^T, so a chunk is eight consecutive words of row n
-        for (int c = tid; c < Lp * (kRf2KC / 8); c += kDelNT) {
-            const int n = ((c >> 6) << 3) | (c & 7), m0 = ((c >> 3) & 7) << 3;
-            float x[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {  // all loads first
-              const int k = kc * kRf2KC + m0 + t;
-              x[t] = (n < L && k < L) ? wsE[(size_t)n * L + k] : 0.f;
-            }
+          for (int u = 0; u < 2; ++u) {
+            const int c = tid + u * kDelNT;
+            const int r = ((c >> 6) << 3) | (c & 7), m0 = ((c >> 3) & 7) << 3;
+            const int i = rb * 128 + r;
+            const float cp = (i < L && sig * s[i] > 0) ? cpl0 : cpl1;
             uint32_t h[4], l[4];
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
-              const float xa = x[t] * sE, xb = x[t + 1] * sE;
+              const float xa = rintf(x[u][t] * cp * sH) * 0x1p-14f, xb = rintf(x[u][t + 1] * cp * sH) * 0x1p-14f;
               h[t / 2] = f32x2_to_f16x2(xa, xb);
               l[t / 2] = f32x2_to_f16x2(xa - f16_lo_to_f32(h[t / 2]), xb - f16_hi_to_f32(h[t / 2]));
             }
-            const uint32_t off = rf_off2(n, m0);
-            unsigned char* bp = sm + 2 * 128 * kRf2KC * 2;
-            *reinterpret_cast<uint4*>(bp + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(bp + bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            const uint32_t off = rf_off2(r, m0);
+            *reinterpret_cast<uint4*>(sm + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(sm + 128 * kRf2KC * 2 + off) = make_uint4(l[0], l[1], l[2], l[3]);
           }
+        }
+        // B: E^T (row n = column n of E, K = rows of E) x 2^se, hi / lo;
+        // wsE holds E^T, so a chunk is eight consecutive words of row n (two
+        // float4 loads: ldE and the offsets are multiples of four); two
+        // chunks per thread in flight
+        const int nc2 = Lp * (kRf2KC / 8);
+        for (int c0 = tid; c0 < nc2; c0 += 2 * kDelNT) {
+          float x[2][8];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int c = c0 + u * kDelNT;
+            const int n = ((c >> 6) << 3) | (c & 7), k0 = kc * kRf2KC + (((c >> 3) & 7) << 3);
+            const bool ok = c < nc2 && n < L;
+            rf_ld8(wsE + (size_t)(ok ? n : 0) * ldE + k0, ok ? ldE - k0 : 0, true, x[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int c = c0 + u * kDelNT;
+            if (c < nc2) {
+              const int n = ((c >> 6) << 3) | (c & 7), m0 = ((c >> 3) & 7) << 3;
+              uint32_t h[4], l[4];
+#pragma unroll
+              for (int t = 0; t < 8; t += 2) {
+                const float xa = x[u][t] * sE, xb = x[u][t + 1] * sE;
+                h[t / 2] = f32x2_to_f16x2(xa, xb);
+                l[t / 2] = f32x2_to_f16x2(xa - f16_lo_to_f32(h[t / 2]), xb - f16_hi_to_f32(h[t / 2]));
+              }
+              const uint32_t off = rf_off2(n, m0);
+              unsigned char* bp = sm + 2 * 128 * kRf2KC * 2;
+              *reinterpret_cast<uint4*>(bp + off) = make_uint4(h[0], h[1], h[2], h[3]);
+              *reinterpret_cast<uint4*>(bp + bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+          }
+        }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -422,27 +469,38 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
           return -1.f;
         }
       }
-      // epilogue: rows rb*128 + 32 q4 + lane, 16 columns per TMEM load
+      // epilogue: rows rb*128 + 32 q4 + lane; columns in groups of eight
+      // (one TMEM load each), two groups 32 apart per pass, loads first
       const int i = rb * 128 + 32 * q4 + lane;
       const bool up = i < L && sig * s[i] > 0;
       const float cp = up ? cpl0 : cpl1, cmh = up ? cmh0 : cmh1, cml = up ? cml0 : cml1;
       float* Gi = G + (size_t)(i < L ? i : 0) * L;
 #pragma unroll 1
-      for (int col0 = 8 * g4; col0 < Lp; col0 += 32) {
-        float q[8], go[8];
+      for (int col0 = 8 * g4; col0 < Lp; col0 += 64) {
+        float q[2][8], go[2][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) go[c] = (i < L && col0 + c < L) ? Gi[col0 + c] : 0.f;  // loads first
-        tmem_ld8(tc->tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)col0, q);
+        for (int u = 0; u < 2; ++u) rf_ld8(Gi + col0 + 32 * u, i < L ? L - col0 - 32 * u : 0, vec, go[u]);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float Hp = rintf(go[c] * cp * sH) * sHi;
-          const float y = Hp + q[c] * sQ;
-          q[c] = fmaf(y, cmh, y * cml);
-          if (i < L && col0 + c < L) drift = fmaxf(drift, fabsf(go[c] - q[c]));
+        for (int u = 0; u < 2; ++u) {
+          if (col0 + 32 * u < Lp) {  // warp-uniform
+            tmem_ld8(tc->tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(col0 + 32 * u), q[u]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) q[u][c] = 0.f;
+          }
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (i < L && col0 + c < L) Gi[col0 + c] = q[c];
+        for (int u = 0; u < 2; ++u) {
+          const int nv = i < L ? L - col0 - 32 * u : 0;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float Hp = rintf(go[u][c] * cp * sH) * sHi;
+            const float y = Hp + q[u][c] * sQ;
+            q[u][c] = fmaf(y, cmh, y * cml);
+            if (c < nv) drift = fmaxf(drift, fabsf(go[u][c] - q[u][c]));
+          }
+          rf_st8(Gi + col0 + 32 * u, nv, vec, q[u]);
+        }
       }
       tc_fence_before();
       __syncthreads();
@@ -456,7 +514,9 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
 
 // G_dn = 1 - G_up^T for a particle-hole symmetric bath (both L x L FP32 in
 // global memory), through per-warp 32 x 33 shared-memory tiles (tile: 16
-// warps x 32 x 33 floats) so that reads and writes are both coalesced.
+// warps x 32 x 33 floats) so that reads and writes are both coalesced.  The
+// rows of a tile go in batches of 16 with every load of a batch (G_up, and
+// the old G_dn for the drift) issued before its stores.
 // Returns max |G_dn(old) - G_dn(new)| (block-wide).  All threads call it.
 __device__ inline float ph_mirror(const float* Gu, float* Gd, int L, float* tile, float* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -466,22 +526,36 @@ __device__ inline float ph_mirror(const float* Gu, float* Gd, int L, float* tile
   float drift = 0.f;
   for (int t = warp; t < nt * nt; t += NW) {
     const int ti = t / nt, tj = t - ti * nt;  // source tile rows ti*32.., columns tj*32..
-    const int c = tj * 32 + lane;
-#pragma unroll 4
-    for (int r = 0; r < 32; ++r) {
-      const int i = ti * 32 + r;
-      tw[r * 33 + lane] = (i < L && c < L) ? Gu[(size_t)i * L + c] : 0.f;
+    const int c = tj * 32 + lane;   // source column
+    const int cc = ti * 32 + lane;  // destination column = source row
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      float v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int i = ti * 32 + h + r;
+        v[r] = (i < L && c < L) ? Gu[(size_t)i * L + c] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) tw[(h + r) * 33 + lane] = v[r];
     }
     __syncwarp();
-    const int cc = ti * 32 + lane;  // destination column = source row
-#pragma unroll 4
-    for (int r = 0; r < 32; ++r) {
-      const int i = tj * 32 + r;      // destination row = source column
-      if (i < L && cc < L) {
-        const float gn = (i == cc ? 1.f : 0.f) - tw[lane * 33 + r];
-        const size_t o = (size_t)i * L + cc;
-        drift = fmaxf(drift, fabsf(Gd[o] - gn));
-        Gd[o] = gn;
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      float o[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int i = tj * 32 + h + r;  // destination row = source column
+        o[r] = (i < L && cc < L) ? Gd[(size_t)i * L + cc] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int i = tj * 32 + h + r;
+        if (i < L && cc < L) {
+          const float gn = (i == cc ? 1.f : 0.f) - tw[lane * 33 + h + r];
+          drift = fmaxf(drift, fabsf(o[r] - gn));
+          Gd[(size_t)i * L + cc] = gn;
+        }
       }
     }
     __syncwarp();
