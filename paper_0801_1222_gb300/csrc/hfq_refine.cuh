@@ -137,8 +137,26 @@ __device__ __forceinline__ void rf_st8(float* p, int n, bool vec, const float* x
   }
 }
 
-__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
-  return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+// The nearest integers ra, rb of a, b (|a|, |b| <= 2^7; ties to even, as
+// rintf) and both as FP16, packed (a in the low half), with full-rate FP32,
+// integer and FP16x2 arithmetic only: adding 1.5 * 2^23 rounds to an integer
+// (the FP32 spacing there is 1), whose bits give v; the FP16 bits of 1536 + v
+// are 0x6600 + v (spacing 1 in [1024, 2048)), and 1536 subtracted in FP16
+// leaves v exactly.
+__device__ __forceinline__ uint32_t rf_round_h2(float a, float b, float* ra, float* rb) {
+  const float ta = a + 12582912.f, tb = b + 12582912.f;
+  *ra = ta - 12582912.f;
+  *rb = tb - 12582912.f;
+  const uint32_t pk = ((0x6600u + (uint32_t)(__float_as_int(ta) - 0x4B400000)) & 0xffffu) |
+                      ((0x6600u + (uint32_t)(__float_as_int(tb) - 0x4B400000)) << 16);
+  const uint32_t c1536 = 0x66006600u;
+  __half2 hv, hc;
+  memcpy(&hv, &pk, 4);
+  memcpy(&hc, &c1536, 4);
+  hv = __hsub2(hv, hc);
+  uint32_t r;
+  memcpy(&r, &hv, 4);
+  return r;
 }
 
 // One spin: G (L x L, row-major, FP32, in global memory) is replaced by its
@@ -233,12 +251,13 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
         unsigned char* dst = sm + b * kRfStage + kRfSlicesA * kRfTileA + rf_off(nl, j8 * 8);
 #pragma unroll
         for (int q = 0; q < kRfSlicesH; ++q) {
-          // slice q: rint of the running remainder, which moves up 7 bits
+          // slice q: the nearest integer v of the running remainder (below
+          // 2^7 in magnitude), which then moves up 7 bits
           uint32_t w[4];
 #pragma unroll
           for (int t = 0; t < 8; t += 2) {
-            const float ra = rintf(y[t]), rb2 = rintf(y[t + 1]);
-            w[t / 2] = pack_h2(ra, rb2);
+            float ra, rb2;
+            w[t / 2] = rf_round_h2(y[t], y[t + 1], &ra, &rb2);
             y[t] = (y[t] - ra) * (float)(1 << kRfBits);
             y[t + 1] = (y[t + 1] - rb2) * (float)(1 << kRfBits);
           }

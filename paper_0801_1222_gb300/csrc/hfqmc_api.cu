@@ -379,8 +379,10 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
       }
       // staging two U blocks per flush group when it fits, else one
       h.ub = delayed_smem(h.L, h.k, false, h.gj_smem, false, 2, h.refine) <= kSmemMax ? 2 : 1;
+      // residency is decided on the sweep's own layout; the refinement's
+      // staging overlays it and may extend it up to the cap
       sm = delayed_smem(h.L, h.k, true, h.gj_smem, false, h.ub, h.refine);
-      h.resident = sm <= kResidentBudget;
+      h.resident = delayed_smem(h.L, h.k, true, h.gj_smem, false, h.ub, false) <= kResidentBudget && sm <= kSmemMax;
       h.gtile = 0;
       if (!h.resident) {
         // flush by TMA reduce-add: G rows must be 16-byte aligned (Lambda % 4

@@ -131,3 +131,25 @@ def test_h_prime_equals_its_slices_at_ties():
     direct = np.rint(np.ldexp(H, 28 - eh)) * 2.0 ** (eh - 28)
     assert np.array_equal(sum(Hs[q] * 2.0 ** (eh - BITS * (q + 1)) for q in range(SH)), direct)
     assert all(np.abs(Hs[0]).max() <= 128 and np.abs(Hs[q]).max() <= 64 for q in range(1, SH))
+
+
+def test_rounding_to_fp16_by_magic_constant():
+    """The H' slicing's rounding (hfq_refine.cuh rf_round_h2), restated in
+    numpy: in FP32, y + 1.5 * 2^23 - 1.5 * 2^23 is the nearest integer of y
+    (ties to even) for |y| <= 2^7; the integer is the FP32 sum's bit pattern
+    minus that of 1.5 * 2^23; 0x6600 + v are the FP16 bits of 1536 + v, and
+    1536 subtracted in FP16 leaves v.  Every multiple of 1/64 in [-128, 128]
+    (ties included) against numpy's rint and float16 (as values: rint keeps
+    the sign of a zero, the subtraction gives +0; the products are the same)."""
+    y = (np.arange(-128 * 64, 128 * 64 + 1) / 64.0).astype(np.float32)
+    magic = np.float32(12582912.0)
+    t = (y + magic).astype(np.float32)
+    r = (t - magic).astype(np.float32)
+    np.testing.assert_array_equal(r, np.rint(y))
+    v = t.view(np.int32).astype(np.int64) - 0x4B400000
+    np.testing.assert_array_equal(v, np.rint(y).astype(np.int64))
+    bits = ((0x6600 + v) & 0xFFFF).astype(np.uint16)
+    h = (bits.view(np.float16) - np.float16(1536.0)).astype(np.float16)
+    np.testing.assert_array_equal(h.astype(np.float64), np.rint(y))
+    nz = np.rint(y) != 0
+    np.testing.assert_array_equal(h.view(np.uint16)[nz], np.rint(y).astype(np.float16).view(np.uint16)[nz])
