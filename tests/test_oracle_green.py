@@ -40,17 +40,31 @@ def test_lambda_definition(orc):
         assert abs(np.cosh(lm) - np.exp(dtau * U / 2)) < 1e-14
 
 
-def test_green_solves_dyson(orc):
-    g0, dtau = _setup(20.0, 100, 5.0)
-    M = orc.bath_matrix(g0)
-    lm = orc.lam(dtau, 5.0)
-    s = orc.init_field(100, 7, 1, 0)
-    for sigma in (1, -1):
-        G, _ = orc.green(M, s, lm, sigma)
-        d = np.exp(sigma * lm * s) - 1.0
-        A = np.eye(100) + (np.eye(100) - M) * d[None, :]
-        ref = np.linalg.solve(A, M)
-        assert np.max(np.abs(G - ref)) < 1e-12
+def test_green_dyson_relation_between_fields(orc):
+    """Hirsch-Fye's Dyson relation ties the Green matrices of two fields s,
+    s' together: G' = G + (G - 1)(e^{V' - V} - 1) G' with V = sigma lambda s.
+    It follows from G^{-1} = (M^{-1} - 1) e^V + 1 and holds for any pair of
+    fields, so the oracle's G for one field is checked against its G for
+    others (a flipped sign of V, or the factors (1 - M) and (e^V - 1) in the
+    other order, break it).  Fields differing in one, a few and half of the
+    slices, both spins, at Lambda = 16 and 100."""
+    rng = np.random.default_rng(5)
+    for beta, L, U in ((8.0, 16, 4.0), (20.0, 100, 5.0)):
+        g0, dtau = _setup(beta, L, U)
+        M = orc.bath_matrix(g0)
+        lm = orc.lam(dtau, U)
+        s = orc.init_field(L, 7, 1, 0)
+        for nflip in (1, 3, L // 2):
+            s2 = s.copy()
+            s2[rng.choice(L, nflip, replace=False)] *= -1
+            for sigma in (1, -1):
+                G, _ = orc.green(M, s, lm, sigma)
+                G2, _ = orc.green(M, s2, lm, sigma)
+                d = np.exp(sigma * lm * (s2 - s)) - 1.0
+                rhs = G + (G - np.eye(L)) @ (d[:, None] * G2)
+                assert np.max(np.abs(G2 - rhs)) < 1e-10 * max(1.0, np.max(np.abs(G2))), (L, nflip, sigma)
+                # the relation is not empty: the two fields' matrices differ
+                assert np.max(np.abs(G2 - G)) > 1e-3
 
 
 @pytest.mark.parametrize("beta,L,U", [(8.0, 16, 4.0), (20.0, 100, 5.0)])
