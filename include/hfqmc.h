@@ -117,10 +117,15 @@ typedef struct {
     double refine_max;  /* REFINE: the largest max |1 - G^{-1} G| for which Newton steps are taken
                            (0 = the default 2^-8; < 0 = never, every recompute from scratch);
                            above 2^-13 a second step follows */
-    int ph_symmetry;    /* F32_DELAYED, REFINE: 0 = when hfqmc_set_G0 finds the bath particle-hole
+    int ph_symmetry;    /* F32_DELAYED, REFINE: a bath that hfqmc_set_G0 finds particle-hole
                            symmetric (G0(tau_k) = G0(beta - tau_k), G0(0+) = -1/2, to 1e-12: half
-                           filling), a recompute refines G_up and sets G_dn = 1 - G_up^T, an identity
-                           every field configuration satisfies then; < 0 = never */
+                           filling) makes G_dn = 1 - G_up^T for every field configuration.
+                           0 = when every grid's bath is symmetric, the sweep keeps G_up only (G_dn's
+                           diagonal, its measured G(tau) and the chain's G_dn at the end of each call
+                           follow from G_up); a grid whose bath is symmetric otherwise refines G_up at
+                           a recompute and sets G_dn = 1 - G_up^T;
+                           1 = only the recompute uses the symmetry (the sweep updates both spins);
+                           < 0 = never */
 } hfqmc_opts;
 
 enum { HFQMC_RECOMPUTE_AUTO = 0, HFQMC_RECOMPUTE_GJ = 1, HFQMC_RECOMPUTE_REFINE = 2 };

@@ -163,11 +163,13 @@ __device__ __forceinline__ void del_factors(float d0, float d1, float gu, float 
 // ---------------------------------------------------------------------------
 // FP32 FMA flush: G^sigma[i][c] += sum_{m<j} U^sigma[i][m] W^sigma[c][m]
 // ---------------------------------------------------------------------------
+// NSP = 1: spin up only (G_dn = 1 - G_up^T is not kept during the sweep).
+template <int NSP = 2>
 __device__ inline void flush_ffma(float* Gu, float* Gd, int ld, const float* Pu, const float* Pw,
                                   int KP, int L, int j) {
   const int T4 = (L + 3) / 4;
   const int tiles = T4 * T4;
-  for (int sp = 0; sp < 2; ++sp) {
+  for (int sp = 0; sp < NSP; ++sp) {
     float* G = sp ? Gd : Gu;
     const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
     const float* W = Pw + (size_t)sp * del_spin_stride(L, KP);
@@ -442,9 +444,12 @@ __device__ __forceinline__ void stage_group(const float* W, int nb, int nN, bool
 // all-zero panel), from the byte-wise maxima each thread kept while
 // appending: exq holds the biased exponents of its largest |u| (byte 0) and
 // |w| (byte 1) for its spin sp (thread parity).  The four bytes of a warp
-// travel in one word of wred (kDelNT / 32 words, one barrier).
+// travel in one word of wred (kDelNT / 32 words, one barrier).  kMirror:
+// only spin up's panels, whose |u| exponents the even threads keep (byte 0)
+// and |w| exponents the odd ones (byte 1).
+template <bool kMirror = false>
 __device__ __forceinline__ void panel_scales(uint32_t exq, uint32_t* wred, int* ea) {
-  uint32_t v = (threadIdx.x & 1) ? (exq << 16) : exq;  // bytes: U up, W up, U down, W down
+  uint32_t v = (!kMirror && (threadIdx.x & 1)) ? (exq << 16) : exq;  // bytes: U up, W up, U down, W down
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = __vmaxu4(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
@@ -505,7 +510,7 @@ __device__ inline bool tc_commit_wait(TcState* tc) {
 // written, and the flush returns once every reduce is complete and visible.  Otherwise (G in shared
 // memory, or the fallback for G in HBM) every thread adds its 64 entries of
 // the tile in place.
-template <bool kTR>
+template <bool kTR, int NSP = 2>
 __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                             const float* Pw, int KP, int L, int j, unsigned char* stage,
                                             const DelLayout& lay, int* status, uint32_t* wred,
@@ -523,8 +528,8 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   const int m = 32 * quarter + lane;               // G column nb + m of a tile
   int nhalf = 0;                                   // half tiles handed to the TMA unit
   int ea[4];
-  panel_scales(exq, wred, ea);
-  for (int sp = 0; sp < 2; ++sp) {
+  panel_scales<NSP == 1>(exq, wred, ea);
+  for (int sp = 0; sp < NSP; ++sp) {
     float* G = sp ? Gd : Gu;
     const float* U = Pu + (size_t)sp * del_spin_stride(L, KP);
     const float* W = Pw + (size_t)sp * del_spin_stride(L, KP);
@@ -624,18 +629,19 @@ __device__ __forceinline__ void flush_tiles(TcState* tc, float* Gu, float* Gd, i
   }
 }
 
+template <int NSP = 2>
 __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, const float* Pu,
                                      const float* Pw, int KP, int L, int j, unsigned char* stage,
                                      const DelLayout& lay, int* status, uint32_t* wred, uint32_t exq,
                                      float* dtile = nullptr, const void* tmap = nullptr, int chain = 0) {
   if (tc->failed) {
-    flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
+    flush_ffma<NSP>(Gu, Gd, ld, Pu, Pw, KP, L, j);
     return;
   }
   if (dtile)
-    flush_tiles<true>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, exq, dtile, tmap, chain);
+    flush_tiles<true, NSP>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, exq, dtile, tmap, chain);
   else
-    flush_tiles<false>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, exq, nullptr, nullptr, 0);
+    flush_tiles<false, NSP>(tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, status, wred, exq, nullptr, nullptr, 0);
 }
 
 // One pass of both spins with RB rows per warp in flight and CPL columns per
@@ -646,12 +652,12 @@ __device__ inline void flush_tcgen05(TcState* tc, float* Gu, float* Gd, int ld, 
 // G is read with plain (coherent) loads: the same kernel writes it through
 // the flush's TMA reduce-adds, so the non-coherent read-only path that
 // const __restrict__ would allow is not valid here.
-template <int RB, int CPL>
+template <int RB, int CPL, int NSP = 2>
 __device__ __forceinline__ void measure_rows_batched(const float* Gu, const float* Gd, int ld, int L,
                                                      float* part) {
   constexpr int NW = kDelNT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int sp = 0; sp < 2; ++sp) {
+  for (int sp = 0; sp < NSP; ++sp) {
     const float* G = sp ? Gd : Gu;
     float* pw = part + (size_t)(sp * NW + warp) * L;
     for (int r0 = warp; r0 < L; r0 += NW * RB) {
@@ -697,7 +703,7 @@ __device__ __forceinline__ void measure_rows_batched(const float* Gu, const floa
 // slot 127 of lane 31, or slot L - 1) by shuffles, and no bin is read or
 // written in shared memory until the warp's range ends: one store per bin
 // into the warp's partial sums (part, pitch L).
-template <int RB>
+template <int RB, int NSP = 2>
 __device__ __forceinline__ void measure_rows_reg(const float* Gu, const float* Gd, int ld, int L,
                                                  float* part) {
   constexpr int NW = kDelNT / 32;
@@ -705,7 +711,7 @@ __device__ __forceinline__ void measure_rows_reg(const float* Gu, const float* G
   const bool two = L > 128;                    // slots of the second block of 128 columns in use
   const int lastc = (L - 1) >> 7, lastl = ((L - 1) & 127) >> 2;  // slot L - 1 (its q is 3)
   const int below = (lane + 31) & 31;
-  for (int sp = 0; sp < 2; ++sp) {
+  for (int sp = 0; sp < NSP; ++sp) {
     const float* G = sp ? Gd : Gu;
     const int rb = (warp * L) / NW, re = ((warp + 1) * L) / NW;
     float acc[2][4];
@@ -786,7 +792,8 @@ __device__ __forceinline__ void measure_rows_reg(const float* Gu, const float* G
 // Everything stays on the FP32 pipe: the caller folds the per-sweep totals
 // into FP64 accumulators.
 // part: 2 * NW * L floats of shared scratch; out[k], out[L+k] receive the
-// sums (not yet divided by L).
+// sums (not yet divided by L).  NSP = 1: spin up only (out[k]).
+template <int NSP = 2>
 __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, int L, float* part,
                                     float* out) {
   constexpr int NW = kDelNT / 32;
@@ -795,13 +802,13 @@ __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, in
   __syncthreads();
   if (L <= 256 && L % 4 == 0 && ld % 4 == 0 &&
       ((reinterpret_cast<uintptr_t>(Gu) | reinterpret_cast<uintptr_t>(Gd)) & 15) == 0) {
-    measure_rows_reg<4>(Gu, Gd, ld, L, part);
+    measure_rows_reg<4, NSP>(Gu, Gd, ld, L, part);
   } else if (L <= 256) {
-    measure_rows_batched<4, 8>(Gu, Gd, ld, L, part);
+    measure_rows_batched<4, 8, NSP>(Gu, Gd, ld, L, part);
   } else if (L <= 512) {
-    measure_rows_batched<2, 16>(Gu, Gd, ld, L, part);
+    measure_rows_batched<2, 16, NSP>(Gu, Gd, ld, L, part);
   } else {
-    for (int sp = 0; sp < 2; ++sp) {
+    for (int sp = 0; sp < NSP; ++sp) {
       const float* G = sp ? Gd : Gu;
       float* pw = part + (size_t)(sp * NW + warp) * L;
       for (int r = warp; r < L; r += NW) {
@@ -818,7 +825,7 @@ __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, in
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 2 * L; e += kDelNT) {
+  for (int e = threadIdx.x; e < NSP * L; e += kDelNT) {
     const int sp = e >= L, k = e - sp * L;
     float acc = 0.f;
     for (int w = 0; w < NW; ++w) acc += part[(size_t)(sp * NW + w) * L + k];
@@ -830,6 +837,7 @@ __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, in
 // The same sums for G in shared memory (odd row pitch ld): thread k walks the
 // wrapped diagonal k of both spins in registers; for a fixed l the threads
 // of a warp read rows l+k at stride ld, i.e. 32 different banks.
+template <int NSP = 2>
 __device__ inline void measure_diagonals(const float* Gu, const float* Gd, int ld, int L, float* out) {
   for (int k = threadIdx.x; k < L; k += kDelNT) {
     float su = 0.f, sd = 0.f;
@@ -837,15 +845,15 @@ __device__ inline void measure_diagonals(const float* Gu, const float* Gd, int l
     for (; l + k < L; ++l) {
       const int o = (l + k) * ld + l;
       su += Gu[o];
-      sd += Gd[o];
+      if (NSP == 2) sd += Gd[o];
     }
     for (; l < L; ++l) {
       const int o = (l + k - L) * ld + l;
       su -= Gu[o];
-      sd -= Gd[o];
+      if (NSP == 2) sd -= Gd[o];
     }
     out[k] = su;
-    out[L + k] = sd;
+    if (NSP == 2) out[L + k] = sd;
   }
   __syncthreads();
 }

@@ -145,6 +145,8 @@ struct SweepArgs {
   int flush;                 // delayed path: 1 tcgen05, 2 FFMA
   int trace_mode;            // 0 none, 1 record the accepted flips, 2 replay them (rank-1 paths)
   int refine;                // delayed path: some grid recomputes by Newton refinement
+  int mirror;                // delayed path: every grid refines and its bath is particle-hole
+                             // symmetric, and the sweep keeps G_up only
 };
 
 constexpr int kTraceOff = 0, kTraceRecord = 1, kTraceReplay = 2;

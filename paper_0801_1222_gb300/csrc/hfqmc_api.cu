@@ -193,6 +193,15 @@ void dev_free(hfqmc_ctx* c, void* p) {
 
 constexpr size_t kMaxGraphs = 8;
 
+// The delayed sweep keeps G_up only when every grid refines and its bath is
+// particle-hole symmetric (and opts.ph_symmetry is 0).
+static int sweep_mirrors(const hfqmc_ctx* c) {
+  if (c->opts.precision != HFQMC_F32_DELAYED || c->opts.ph_symmetry != 0) return 0;
+  for (int g = 0; g < c->n_grids; ++g)
+    if (!c->gh[g].refine || !c->gc[g].ph) return 0;
+  return 1;
+}
+
 void drop_graphs(hfqmc_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
@@ -218,6 +227,7 @@ int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
   a.refine = 0;
   for (int g = 0; g < c->n_grids; ++g)
     if (c->gh[g].refine && c->gh[g].lambda != 0.0) a.refine = 1;
+  a.mirror = sweep_mirrors(c);
   if (c->opts.precision == HFQMC_F32_DELAYED)
     return launch_sweep_delayed(a, c->sweep_ctas, c->sweep_smem, c->stream);
   return launch_sweep_rank1(f64_path(c), a, c->sweep_ctas, c->sweep_smem, c->stream);
@@ -685,7 +695,9 @@ int hfqmc_set_G0(hfqmc_ctx* c, int grid, const double* G0_tau) {
     ph = dev <= 1e-12;
   }
   if (ph != c->gc[grid].ph) {
+    const int was = sweep_mirrors(c);
     c->gc[grid].ph = ph;
+    if (sweep_mirrors(c) != was) drop_graphs(c);  // the sweep's kernel variant changes
     CK(cudaMemcpyAsync(c->d_grids + grid, &c->gc[grid], sizeof(GridConst), cudaMemcpyHostToDevice, c->stream));
   }
   double* dM = const_cast<double*>(c->gc[grid].M);

@@ -42,7 +42,13 @@ constexpr int kNoSlice = 0x7fffffff;
 // RefineConst) before Gauss-Jordan; without it the kernel carries only the
 // Gauss-Jordan recompute (the refinement's code costs the accept loop some
 // registers, so contexts that never refine launch the variant without it).
-template <bool kRecord, bool kRefine>
+// kMirror (every grid's bath particle-hole symmetric, so G_dn = 1 - G_up^T
+// for every field): the sweep keeps G_up only.  A thread pair owns a row of
+// G_up: the even thread appends its column entry u_i, the odd one its row
+// entry w_i, and they swap them by one shuffle; G_dn's diagonal is 1 minus
+// G_up's, its measured sums follow from G_up's (diagonal L - k for k > 0),
+// and the chain's G_dn is written as 1 - G_up^T when the chain ends.
+template <bool kRecord, bool kRefine, bool kMirror = false>
 __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   constexpr int NT = kDelNT;
   constexpr int NW = NT / 32;
@@ -120,9 +126,9 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     float dg[kRowsPerThread], uv[kRowsPerThread];
     int sv[kRowsPerThread];
     bool lastbad[kRowsPerThread];
-    float* Gs = sp ? Gd : Gu;
-    float* Us = Pu + (size_t)sp * del_spin_stride(L, KP);
-    float* Ws = Pw + (size_t)sp * del_spin_stride(L, KP);
+    float* Gs = (sp && !kMirror) ? Gd : Gu;
+    float* Us = Pu + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
+    float* Ws = Pw + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
     auto load_diag = [&]() {
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
@@ -162,10 +168,10 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     auto flush = [&]() {
       if (j == 0) return;
       if (use_tc)
-        flush_tcgen05(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status,
-                      reinterpret_cast<uint32_t*>(red), exq, dtile, gc.tmapG, ip.chain);
+        flush_tcgen05<kMirror ? 1 : 2>(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status,
+                                       reinterpret_cast<uint32_t*>(red), exq, dtile, gc.tmapG, ip.chain);
       else
-        flush_ffma(Gu, Gd, ld, Pu, Pw, KP, L, j);
+        flush_ffma<kMirror ? 1 : 2>(Gu, Gd, ld, Pu, Pw, KP, L, j);
       __syncthreads();
       load_diag();
       j = 0;
@@ -186,9 +192,15 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
         if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
         const int r = row0 + qq * kRowStride;
-        const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
-        const float gu = sp ? other : dg[qq];
-        const float gd = sp ? dg[qq] : other;
+        float gu, gd;
+        if constexpr (kMirror) {
+          gu = dg[qq];  // both threads of the pair hold G_up's diagonal
+          gd = 1.f - gu;
+        } else {
+          const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
+          gu = sp ? other : dg[qq];
+          gd = sp ? dg[qq] : other;
+        }
         bool acc = false, bad = false;
         if (r < L && r >= lo) {
           acc = del_decide(d0, d1, gu, gd, sv[qq], uv[qq], rule, &bad);
@@ -244,6 +256,54 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         fd = fac[2 * l + 1];
       }
       while (l < L) {
+        if constexpr (kMirror) {
+          // spin up only: the even thread of a pair appends u_i (column l),
+          // the odd one w_i (row l); one shuffle gives both the pair's values
+          float gq[kRowsPerThread];
+#pragma unroll
+          for (int qq = 0; qq < kRowsPerThread; ++qq) {
+            if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
+            const int i = row0 + qq * kRowStride;
+            gq[qq] = i < L ? (sp ? Gs[l * ld + i] : Gs[i * ld + l]) : 0.f;
+          }
+#pragma unroll
+          for (int qq = 0; qq < kRowsPerThread; ++qq) {
+            if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
+            const int i = row0 + qq * kRowStride;
+            const int oi = i * KP, ol = l * KP;  // 32-bit shared-memory offsets
+            float c4[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < L) {
+              const float4* Ar = reinterpret_cast<const float4*>(Us + (sp ? ol : oi));
+              const float4* Br = reinterpret_cast<const float4*>(Ws + (sp ? oi : ol));
+              const int j4 = (j + 3) >> 2;
+              for (int m4 = 0; m4 < j4; ++m4) {
+                const float4 a1 = Ar[m4], b1 = Br[m4];
+                c4[0] = __fmaf_rn(a1.x, b1.x, c4[0]);
+                c4[1] = __fmaf_rn(a1.y, b1.y, c4[1]);
+                c4[2] = __fmaf_rn(a1.z, b1.z, c4[2]);
+                c4[3] = __fmaf_rn(a1.w, b1.w, c4[3]);
+              }
+            }
+            const float dot = gq[qq] + ((c4[0] + c4[1]) + (c4[2] + c4[3]));
+            const float mine = i >= L ? 0.f : sp ? dot * fu : dot - ((i == l) ? 1.f : 0.f);
+            const float theirs = __shfl_xor_sync(0xffffffffu, mine, 1);
+            if (i < L) {
+              const float uu = sp ? theirs : mine, ww = sp ? mine : theirs;
+              if (sp) {
+                exq = __vmaxu4(exq, ((__float_as_uint(ww) << 1) >> 24) << 8);
+                Ws[oi + j] = ww;
+              } else {
+                exq = __vmaxu4(exq, (__float_as_uint(uu) << 1) >> 24);
+                Us[oi + j] = uu;
+              }
+              dg[qq] = __fmaf_rn(uu, ww, dg[qq]);
+              if (i == l) {
+                sv[qq] = -sv[qq];
+                if (sp == 0) ss[i] = (int8_t)sv[qq];
+              }
+            }
+          }
+        } else {
         // append column j of the panels for the owned rows of this thread's spin
         const float f = sp ? fd : fu;
         // base G entries of every owned row first (before any panel store), so
@@ -291,6 +351,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             if (sp == 0) ss[i] = (int8_t)sv[qq];
           }
         }
+        }
         hash = (hash ^ (unsigned long long)(t * (long long)L + l)) * kFnvPrime;
         if constexpr (kRecord) {
           if (tid == 0) ip.trace[(size_t)sw * trace_words(L) + (l >> 5)] |= 1u << (l & 31);
@@ -324,12 +385,14 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             float* rws = reinterpret_cast<float*>(ip.ws);
             float* rred = reinterpret_cast<float*>(red);
             const float d0 = refine_spin(gc, *gc.rc, ss, 1, Ggl, rws, smem + lay.off_rf, &tc, rred, a.status, &steps);
-            // spin down: mirrored for a particle-hole symmetric bath, else refined too
+            // spin down: not kept during a mirrored sweep; mirrored for a
+            // particle-hole symmetric bath, else refined too
             const float d1 = d0 < 0.f ? -1.f
-                             : gc.ph ? ph_mirror(Ggl, Ggl + (size_t)L * L, L,
-                                                 reinterpret_cast<float*>(smem + lay.off_rf), rred)
-                                     : refine_spin(gc, *gc.rc, ss, -1, Ggl + (size_t)L * L, rws, smem + lay.off_rf,
-                                                   &tc, rred, a.status, &steps);
+                             : kMirror ? 0.f
+                             : gc.ph   ? ph_mirror(Ggl, Ggl + (size_t)L * L, L,
+                                                   reinterpret_cast<float*>(smem + lay.off_rf), rred)
+                                       : refine_spin(gc, *gc.rc, ss, -1, Ggl + (size_t)L * L, rws, smem + lay.off_rf,
+                                                     &tc, rred, a.status, &steps);
             if (d0 >= 0.f && d1 >= 0.f)
               d = fmax((double)d0, (double)d1);
             else
@@ -340,7 +403,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             // scratch overlays the idle part of shared memory (never G)
             d = recompute_green_inv<float, NT, true>(
                 gc, ss, in_hbm ? Ggl : Gu, in_hbm ? Ggl + (size_t)L * L : Gd, in_hbm ? L : ld, ip.ws, red, redi,
-                &s_inv, &s_piv, colk, perm, true, a.status, 0, 2, reinterpret_cast<double*>(smem + lay.off_gjb));
+                &s_inv, &s_piv, colk, perm, true, a.status, 0, kMirror ? 1 : 2,
+                reinterpret_cast<double*>(smem + lay.off_gjb));
           }
           if (in_hbm) {
             for (int i = warp; i < 2 * L; i += NW)
@@ -365,11 +429,15 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         float* part = reinterpret_cast<float*>(smem + lay.off_stage);
         float* gsum = reinterpret_cast<float*>(smem + lay.off_U);
         if (resident)
-          measure_diagonals(Gu, Gd, ld, L, gsum);
+          measure_diagonals<kMirror ? 1 : 2>(Gu, Gd, ld, L, gsum);
         else
-          measure_rows(Gu, Gd, ld, L, part, gsum);
+          measure_rows<kMirror ? 1 : 2>(Gu, Gd, ld, L, part, gsum);
         for (int k = tid; k < L; k += NT) {
-          const double gu = (double)gsum[k] / (double)L, gd = (double)gsum[L + k] / (double)L;
+          const double gu = (double)gsum[k] / (double)L;
+          // G_dn = 1 - G_up^T: its sum of diagonal k > 0 is G_up's sum of
+          // diagonal L - k, of diagonal 0 it is L minus G_up's
+          const double gd = kMirror ? (k == 0 ? (double)L - (double)gsum[0] : (double)gsum[L - k]) / (double)L
+                                    : (double)gsum[L + k] / (double)L;
           // the three accumulators loaded before any is stored: one L2 round trip
           double* bk = ip.bins + (size_t)b * L;
           const double a0 = ip.acc[k], a1 = ip.acc[L + k], b0 = bk[k];
@@ -382,7 +450,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
         for (int qq = 0; qq < kRowsPerThread; ++qq) {
           if (qq * kRowStride >= L) break;  // uniform: rows beyond the grid
           const float other = __shfl_xor_sync(0xffffffffu, dg[qq], 1);
-          if (sp == 0 && row0 + qq * kRowStride < L) v += (1.f - dg[qq]) * (1.f - other);
+          const float dn = kMirror ? dg[qq] : 1.f - other;  // 1 - G_dn,ii
+          if (sp == 0 && row0 + qq * kRowStride < L) v += (1.f - dg[qq]) * dn;
         }
         __syncthreads();  // every thread has read its totals
         for (int e = tid; e < 2 * L; e += NT) gsum[e] = 0.f;
@@ -400,6 +469,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     if (resident) {
       for (int i = warp; i < 2 * L; i += NW)
         for (int jj = lane; jj < L; jj += 32) Ggl[(size_t)i * L + jj] = Gu[(size_t)i * ld + jj];
+    }
+    if constexpr (kMirror) {
+      // the chain's G_dn for the host and the next call: 1 - G_up^T
+      __syncthreads();
+      (void)ph_mirror(Ggl, Ggl + (size_t)L * L, L, reinterpret_cast<float*>(smem + lay.off_rf),
+                      reinterpret_cast<float*>(red));
     }
     for (int l = tid; l < L; l += NT) ip.s[l] = ss[l];
     // bad ratios were counted per owned row: sum over the CTA
@@ -433,7 +508,7 @@ size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int u
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
   cudaError_t e = cudaSuccess;
   for (auto* f : {k_sweep_delayed<false, false>, k_sweep_delayed<true, false>, k_sweep_delayed<false, true>,
-                  k_sweep_delayed<true, true>})
+                  k_sweep_delayed<true, true>, k_sweep_delayed<false, true, true>, k_sweep_delayed<true, true, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (e == cudaSuccess)
@@ -446,7 +521,9 @@ int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
 
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st) {
   const bool rec = a.trace_mode == kTraceRecord;
-  if (a.refine)
+  if (a.refine && a.mirror)
+    (rec ? k_sweep_delayed<true, true, true> : k_sweep_delayed<false, true, true>)<<<ctas, kDelNT, smem, st>>>(a);
+  else if (a.refine)
     (rec ? k_sweep_delayed<true, true> : k_sweep_delayed<false, true>)<<<ctas, kDelNT, smem, st>>>(a);
   else
     (rec ? k_sweep_delayed<true, false> : k_sweep_delayed<false, false>)<<<ctas, kDelNT, smem, st>>>(a);

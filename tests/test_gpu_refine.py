@@ -119,7 +119,9 @@ def test_paired_G_tau_with_refine_at_nwrap_64():
 
 def test_particle_hole_mirror_and_both_spins_refined(orc):
     """A particle-hole symmetric bath (the Bethe bath at half filling) turns
-    the mirror on: the recompute refines G_up and sets G_dn = 1 - G_up^T.  With
+    the mirror on: with ph_symmetry = 0 the sweep keeps G_up only (G_dn =
+    1 - G_up^T written when the call ends), with 1 the sweep updates both
+    spins and the recompute refines G_up and sets G_dn = 1 - G_up^T.  With
     ph_symmetry = -1, or for a bath that is not symmetric, both spins are
     refined.  Every variant leaves G_up and G_dn within 4x FP32 rounding of the
     oracle's fresh FP64 inverses (n_wrap = 1)."""
@@ -129,7 +131,7 @@ def test_particle_hole_mirror_and_both_spins_refined(orc):
     sym = inputs.bethe_G0_tau(beta, L)
     tau = np.arange(L) * beta / L
     asym = sym + 2e-3 * np.sin(2 * np.pi * tau / beta)  # G0(tau) != G0(beta - tau)
-    for g0, phs, expect in ((sym, 0, 1), (sym, -1, 0), (asym, 0, 0)):
+    for g0, phs, expect in ((sym, 0, 1), (sym, 1, 1), (sym, -1, 0), (asym, 0, 0)):
         ctx = h.HFQMC(beta, U, [beta / L], [2], seed=4, precision="f32_delayed", n_wrap=1,
                       drift_fail=1.0, recompute="refine", ph_symmetry=phs)
         ctx.set_G0(0, g0)
@@ -144,3 +146,76 @@ def test_particle_hole_mirror_and_both_spins_refined(orc):
                 Gx, _ = orc.green(M, ch["s"], lam, sig)
                 assert np.max(np.abs(G - Gx)) <= 4.0 * _fp32_rounding(Gx) + 1e-9, (phs, expect, c, sig)
         ctx.close()
+
+
+@pytest.mark.parametrize("L,beta,chains", [(100, 20.0, 4), (240, 40.0, 3), (37, 10.0, 4)])
+def test_mirrored_sweep_follows_the_oracle(orc, L, beta, chains):
+    """The sweep that keeps G_up only (every grid's bath particle-hole
+    symmetric, ph_symmetry = 0) against the one that updates both spins
+    (ph_symmetry = 1) and the FP64 oracle, same seeds, N_wrap 64 with the
+    refinement: G on chip (Lambda = 100), in HBM (240), ragged (37).  The
+    chains that took the oracle's decisions hold G_up within the FP32 drift of
+    64 flips of it, G_dn = 1 - G_up^T bit for bit (written as 1 - x in FP32),
+    and the measured G(tau) and D within the drift of the two-spin sweep's."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    res = {}
+    for phs in (0, 1):
+        ctx, qp = make_pair(orc, beta, [(5.0, beta / L)], [chains], precision="f32_delayed", n_wrap=64,
+                            drift_fail=1.0, recompute="refine", ph_symmetry=phs)
+        ctx.sweep(1, 2)
+        if phs == 0:
+            q = qp  # the oracle the mirrored sweep is compared with
+            q.sweep(1, 2)
+        st = ctx.get_stats(0)
+        assert st["ph_symmetric"] == 1 and st["recompute_fallbacks"] == 0 and st["drift_max"] < 1e-3
+        res[phs] = (ctx.get_G(0), ctx.get_D(0), [ctx.get_chain(0, c) for c in range(chains)])
+        ctx.close()
+    same = 0
+    for c, och in enumerate(q.chains[0]):
+        ch = res[0][2][c]
+        np.testing.assert_array_equal(ch["Gdn"].astype(np.float32),
+                                      (np.eye(L, dtype=np.float32) - ch["Gup"].astype(np.float32).T))
+        if ch["hash"] == och.decision_hash:
+            same += 1
+            assert np.abs(ch["Gup"] - och.Gup).max() < 1e-3
+            assert np.abs(ch["Gdn"] - och.Gdn).max() < 1e-3
+    assert same >= 2
+    # the two sweeps follow the same decisions as long as their FP32 rounding allows;
+    # chains that agree give the same measured G(tau) to the drift
+    agree = [c for c in range(chains) if res[0][2][c]["hash"] == res[1][2][c]["hash"]]
+    assert len(agree) >= 2
+    for c in agree:
+        a, b = res[0][2][c], res[1][2][c]
+        assert np.abs(a["acc"] - b["acc"]).max() < 1e-3
+
+
+def test_mirror_turns_off_when_a_bath_loses_its_symmetry(orc):
+    """set_G0 with an asymmetric bath on one grid of two switches the sweep
+    back to both spins (the cached graph of the mirrored sweep is dropped):
+    the decisions then follow the oracle's with that bath, and G_dn is no
+    longer 1 - G_up^T."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    beta, L = 20.0, 100
+    grids = [(5.0, beta / L), (5.0, beta / L)]
+    ctx, q = make_pair(orc, beta, grids, [3, 3], precision="f32_delayed", n_wrap=64, drift_fail=1.0,
+                       recompute="refine")
+    ctx.sweep(0, 2)  # mirrored sweep, graph captured
+    q.sweep(0, 2)
+    tau = np.arange(L) * beta / L
+    asym = inputs.bethe_G0_tau(beta, L) + 2e-3 * np.sin(2 * np.pi * tau / beta)
+    ctx.set_G0(1, asym)
+    q.set_G0(1, asym)
+    assert ctx.get_stats(0)["ph_symmetric"] == 1 and ctx.get_stats(1)["ph_symmetric"] == 0
+    ctx.sweep(0, 2)
+    q.sweep(0, 2)
+    same = 0
+    for c, och in enumerate(q.chains[1]):
+        ch = ctx.get_chain(1, c)
+        if ch["hash"] == och.decision_hash:
+            same += 1
+            assert np.abs(ch["Gdn"] - och.Gdn).max() < 1e-3
+        assert np.abs(ch["Gdn"] - (np.eye(L) - ch["Gup"].T)).max() > 1e-4
+    assert same >= 1
+    ctx.close()
