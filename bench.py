@@ -40,8 +40,9 @@ L2_FLUSH_BYTES = 512 << 20
 # the earlier per-Lambda table with long recompute intervals, for comparison
 LONG_NWRAP_TABLE = [(64, 32, 8192), (128, 32, 8192), (144, 32, 16384), (176, 24, 16384), (1024, 16, 16384)]
 # dram read + write of one full-size launch (1000 sweeps of the multigrid
-# workload at N_wrap 64), from a one-pass ncu capture of this kernel
-TRAFFIC_PER_1000_SWEEPS = 5503224832 + 101613540096
+# workload at N_wrap 64), from a one-pass ncu capture of this kernel (None
+# while the kernel has changed since)
+TRAFFIC_PER_1000_SWEEPS = 273900032 + 22646633216
 
 
 def parse():
