@@ -447,7 +447,10 @@ def run_dmft(args, rank, world, local):
     ctx = hfqmc.HFQMC(beta, [g[0] for g in grids], [g[1] for g in grids], [g[3] for g in grids],
                       seed=1 + rank, precision=args.precision, k=args.k, n_wrap=args.n_wrap, flush=args.flush,
                       drift_fail=1.0, stream=stream, recompute=args.recompute)
-    loop = dmft.BatchedMultigridDMFT(ctx, beta, w["U"], [beta / L for L in w["L"]], n_fine=1001, n_iw=4096)
+    # half filling: the baths are made exactly particle-hole symmetric, so the
+    # sweep keeps G_up only
+    loop = dmft.BatchedMultigridDMFT(ctx, beta, w["U"], [beta / L for L in w["L"]], n_fine=1001, n_iw=4096,
+                                     ph_symmetric=True)
     pps = proposals_per_sweep(grids)
     first, later = w["sweeps"][0], w["sweeps_later"][0]
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")

@@ -76,13 +76,30 @@ def extrapolate_scalar(dtaus, values, errors=None):
     return float(a[0]), float(sa[0])
 
 
+def ph_symmetrize(g):
+    """A bath sampled at tau_k = k beta / L made exactly particle-hole
+    symmetric: G0(tau_k) and G0(tau_{L-k}) replaced by their mean (the same
+    floating-point value for both), G0(0+) = -1/2.  At half filling the exact
+    bath has this symmetry; the Monte Carlo noise of a DMFT update breaks it
+    slightly."""
+    g = np.array(g, dtype=np.float64)
+    L = g.shape[0]
+    k = np.arange(1, L)
+    out = g.copy()
+    out[k] = 0.5 * (g[k] + g[L - k])
+    out[0] = -0.5
+    return out
+
+
 class MultigridDMFT:
     """Multigrid HF-QMC DMFT on the Bethe lattice.  ``solver`` is an
     ``hfqmc.HFQMC`` context (or anything with its set_G0 / sweep / get_G /
     get_D calls, e.g. the oracle) over the grids ``dtaus`` of one U, starting
-    at grid index ``grid0`` of the solver."""
+    at grid index ``grid0`` of the solver.  ``ph_symmetric``: every bath
+    sampled on a grid is made exactly particle-hole symmetric (half filling;
+    the library then keeps G_up only)."""
 
-    def __init__(self, solver, beta, dtaus, n_fine=1001, n_iw=4096, mix=1.0, grid0=0):
+    def __init__(self, solver, beta, dtaus, n_fine=1001, n_iw=4096, mix=1.0, grid0=0, ph_symmetric=False):
         self.solver = solver
         self.beta = float(beta)
         self.dtaus = list(dtaus)
@@ -92,10 +109,12 @@ class MultigridDMFT:
         self.mix = mix
         self.grid0 = int(grid0)
         self.G0_iw = inputs.bethe_G0_iw(1j * matsubara(self.beta, n_iw))
+        self.ph_symmetric = bool(ph_symmetric)
         self.history = []
 
     def bath_on_grid(self, L):
-        return bath_tau(self.beta, np.arange(L) * self.beta / L, self.G0_iw)
+        g = bath_tau(self.beta, np.arange(L) * self.beta / L, self.G0_iw)
+        return ph_symmetrize(g) if self.ph_symmetric else g
 
     def set_baths(self):
         """The current bath, sampled on every grid of this loop."""
@@ -132,11 +151,12 @@ class BatchedMultigridDMFT:
     all baths, runs one sweep call over every chain of every (U, dtau) grid,
     then updates each U's bath from its own grids."""
 
-    def __init__(self, solver, beta, Us, dtaus, n_fine=1001, n_iw=4096, mix=1.0):
+    def __init__(self, solver, beta, Us, dtaus, n_fine=1001, n_iw=4096, mix=1.0, ph_symmetric=False):
         self.solver = solver
         self.Us = list(Us)
         self.loops = [MultigridDMFT(solver, beta, dtaus, n_fine=n_fine, n_iw=n_iw, mix=mix,
-                                    grid0=u * len(dtaus)) for u in range(len(self.Us))]
+                                    grid0=u * len(dtaus), ph_symmetric=ph_symmetric)
+                      for u in range(len(self.Us))]
 
     def iterate(self, n_warm, n_meas):
         for lp in self.loops:

@@ -76,8 +76,9 @@ def test_batched_multi_U_dmft_matches_the_oracle_solver(orc):
 
 def test_config5_shape_one_short_iteration():
     """Four U values x six grids (Lambda 80 .. 320), 1024 chains in one FP32
-    delayed context: one DMFT iteration with a few sweeps; every U's bath
-    update is finite and D lies in (0, 1/4), decreasing with U."""
+    delayed context: two DMFT iterations with a few sweeps and particle-hole
+    symmetric baths (so every grid keeps G_up only); every U's bath update is
+    finite and D lies in (0, 1/4), decreasing with U."""
     from paper_0801_1222_gb300 import dmft, inputs
     h = lib()
     w = inputs.WORKLOADS["dmft_c5"]
@@ -86,12 +87,14 @@ def test_config5_shape_one_short_iteration():
     beta = w["beta"]
     ctx = h.HFQMC(beta, [g[0] for g in grids], [g[1] for g in grids], [g[3] for g in grids], seed=1,
                   precision="f32_delayed", drift_fail=1.0)
-    loop = dmft.BatchedMultigridDMFT(ctx, beta, w["U"], [beta / L for L in w["L"]], n_fine=801, n_iw=2048)
-    recs = loop.iterate(5, 20)
+    loop = dmft.BatchedMultigridDMFT(ctx, beta, w["U"], [beta / L for L in w["L"]], n_fine=801, n_iw=2048,
+                                     ph_symmetric=True)
+    loop.iterate(5, 20)
+    recs = loop.iterate(5, 20)  # the updated baths, made particle-hole symmetric, keep G_up only
     Ds = [r["D"] for r in recs]
     assert all(np.all(np.isfinite(lp.G0_iw)) for lp in loop.loops)
     assert all(0.0 < d < 0.25 for d in Ds) and Ds[0] > Ds[-1]
     for g in range(24):
         st = ctx.get_stats(g)
-        assert st["n_wrap"] == 64 and st["accepted"] > 0
+        assert st["n_wrap"] == 64 and st["accepted"] > 0 and st["ph_symmetric"] == 1
     ctx.close()
