@@ -227,7 +227,9 @@ int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
   a.refine = 0;
   for (int g = 0; g < c->n_grids; ++g)
     if (c->gh[g].refine && c->gh[g].lambda != 0.0) a.refine = 1;
-  a.mirror = sweep_mirrors(c);
+  // the G_up-only variant exists for the refining kernel only (a context
+  // whose grids all have lambda = 0 runs the plain two-spin kernel)
+  a.mirror = a.refine ? sweep_mirrors(c) : 0;
   if (c->opts.precision == HFQMC_F32_DELAYED)
     return launch_sweep_delayed(a, c->sweep_ctas, c->sweep_smem, c->stream);
   return launch_sweep_rank1(f64_path(c), a, c->sweep_ctas, c->sweep_smem, c->stream);
