@@ -127,8 +127,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     int sv[kRowsPerThread];
     bool lastbad[kRowsPerThread];
     float* Gs = (sp && !kMirror) ? Gd : Gu;
+    // G_up only: W starts 16 floats past the panel block (inside the unused
+    // second spin's space), so row r of U and row r of W lie in different
+    // shared-memory banks (see the append)
+    float* const Pw1 = kMirror ? Pw + 16 : Pw;
     float* Us = Pu + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
-    float* Ws = Pw + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
+    float* Ws = Pw1 + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
     auto load_diag = [&]() {
 #pragma unroll
       for (int qq = 0; qq < kRowsPerThread; ++qq) {
@@ -168,10 +172,10 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     auto flush = [&]() {
       if (j == 0) return;
       if (use_tc)
-        flush_tcgen05<kMirror ? 1 : 2>(&tc, Gu, Gd, ld, Pu, Pw, KP, L, j, stage, lay, a.status,
+        flush_tcgen05<kMirror ? 1 : 2>(&tc, Gu, Gd, ld, Pu, Pw1, KP, L, j, stage, lay, a.status,
                                        reinterpret_cast<uint32_t*>(red), exq, dtile, gc.tmapG, ip.chain);
       else
-        flush_ffma<kMirror ? 1 : 2>(Gu, Gd, ld, Pu, Pw, KP, L, j);
+        flush_ffma<kMirror ? 1 : 2>(Gu, Gd, ld, Pu, Pw1, KP, L, j);
       __syncthreads();
       load_diag();
       j = 0;
@@ -273,8 +277,12 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
             const int oi = i * KP, ol = l * KP;  // 32-bit shared-memory offsets
             float c4[4] = {0.f, 0.f, 0.f, 0.f};
             if (i < L) {
-              const float4* Ar = reinterpret_cast<const float4*>(Us + (sp ? ol : oi));
-              const float4* Br = reinterpret_cast<const float4*>(Ws + (sp ? oi : ol));
+              // even lane: U row i . W row l; odd lane: W row i . U row l.  The
+              // first load reads a distinct row in every lane (U or W, whose
+              // rows of one index sit 16 banks apart), the second the pair's
+              // two shared rows: both conflict-free
+              const float4* Ar = reinterpret_cast<const float4*>((sp ? Ws : Us) + oi);
+              const float4* Br = reinterpret_cast<const float4*>((sp ? Us : Ws) + ol);
               const int j4 = (j + 3) >> 2;
               for (int m4 = 0; m4 < j4; ++m4) {
                 const float4 a1 = Ar[m4], b1 = Br[m4];
