@@ -389,12 +389,21 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
 
     // ---- GEMM2: G_new = (1 + D)^{-1} (H' + H' E), 128 rows x all columns ----
     const int Lp = rf_pad(L, 16), nkc2 = rf_pad(L, kRf2KC) / kRf2KC;
-    const uint32_t a2 = sm0, b2 = sm0 + 2u * 128u * kRf2KC * 2u;
     const uint32_t bl = (uint32_t)Lp * kRf2KC * 2u;  // bytes of one E^T part (hi or lo)
+    constexpr uint32_t kAbuf = 2u * 128u * kRf2KC * 2u;  // one row block's H' hi and lo
     const float sH = pow2f(28 - eh);                // H' = rint(H 2^{28-eh}) 2^{eh-28}
     const float sE = pow2f(se), sHi = pow2f(eh - 28), sQ = pow2f(eh - 14 - se);
-    for (int rb = 0; rb < nrb; ++rb) {
+    // two row blocks of 128 and at most 256 columns: both blocks' products at
+    // once (accumulators at TMEM columns 0 and 256), so each E^T chunk is
+    // staged once; else one row block at a time
+    const int nr = (nrb == 2 && Lp <= 256) ? 2 : 1;
+    const uint32_t b2 = sm0 + (uint32_t)nr * kAbuf;
+    for (int rb0 = 0; rb0 < nrb; rb0 += nr) {
       for (int kc = 0; kc < nkc2; ++kc) {
+#pragma unroll 1
+        for (int ur = 0; ur < nr; ++ur) {
+        const int rb = rb0 + ur;
+        unsigned char* sa = sm + ur * kAbuf;
         // A: H' of rows rb*128.. (x 2^{14-eh}, below 2^14), hi / lo: 1024
         // chunks of eight K values, two per thread, the loads of both first.
         // chunk c: row ((c >> 6) << 3) | (c & 7), K offset ((c >> 3) & 7) * 8, so
@@ -422,9 +431,10 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
               l[t / 2] = f32x2_to_f16x2(xa - f16_lo_to_f32(h[t / 2]), xb - f16_hi_to_f32(h[t / 2]));
             }
             const uint32_t off = rf_off2(r, m0);
-            *reinterpret_cast<uint4*>(sm + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(sm + 128 * kRf2KC * 2 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            *reinterpret_cast<uint4*>(sa + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(sa + 128 * kRf2KC * 2 + off) = make_uint4(l[0], l[1], l[2], l[3]);
           }
+        }
         }
         // B: E^T (row n = column n of E, K = rows of E) x 2^se, hi / lo;
         // wsE holds E^T, so a chunk is eight consecutive words of row n (two
@@ -453,7 +463,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
                 l[t / 2] = f32x2_to_f16x2(xa - f16_lo_to_f32(h[t / 2]), xb - f16_hi_to_f32(h[t / 2]));
               }
               const uint32_t off = rf_off2(n, m0);
-              unsigned char* bp = sm + 2 * 128 * kRf2KC * 2;
+              unsigned char* bp = sm + nr * kAbuf;
               *reinterpret_cast<uint4*>(bp + off) = make_uint4(h[0], h[1], h[2], h[3]);
               *reinterpret_cast<uint4*>(bp + bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
             }
@@ -465,14 +475,17 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
         if (tid == 0) {
           tc_fence_after();
 #pragma unroll 1
+          for (int ur = 0; ur < nr; ++ur)
+#pragma unroll 1
           for (int half = 0; half * 256 < Lp; ++half) {
             const int Nh = Lp - half * 256 < 256 ? Lp - half * 256 : 256;
             const uint32_t idesc2 = make_idesc_f16(Nh);
             const uint32_t bo = (uint32_t)half * 32u * 1024u;  // 256 rows of B: 32 groups of 8 x 1024 B
+            const uint32_t a2 = sm0 + (uint32_t)ur * kAbuf;
 #pragma unroll 1
             for (int kk = 0; kk < kRf2KC / 16; ++kk) {
               const uint32_t ko = (uint32_t)kk * 256u;
-              const uint32_t d = tc->tmem + (uint32_t)(half * 256);
+              const uint32_t d = tc->tmem + (uint32_t)((ur + half) * 256);
               const uint64_t ahi = make_smem_desc(a2 + ko, 128u, (kRf2KC / 8) * 128u);
               const uint64_t bhi = make_smem_desc(b2 + bo + ko, 128u, (kRf2KC / 8) * 128u);
               tc_mma_f16(d, ahi, bhi, idesc2, (kc > 0 || kk > 0) ? 1 : 0);
@@ -488,8 +501,12 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
           return -1.f;
         }
       }
-      // epilogue: rows rb*128 + 32 q4 + lane; columns in groups of eight
+      // epilogue: rows rb*128 + 32 q4 + lane of each row block of the group
+      // (its accumulator at TMEM column 256 ur); columns in groups of eight
       // (one TMEM load each), two groups 32 apart per pass, loads first
+#pragma unroll 1
+      for (int ur = 0; ur < nr; ++ur) {
+      const int rb = rb0 + ur;
       const int i = rb * 128 + 32 * q4 + lane;
       const bool up = i < L && sig * s[i] > 0;
       const float cp = up ? cpl0 : cpl1, cmh = up ? cmh0 : cmh1, cml = up ? cml0 : cml1;
@@ -502,7 +519,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           if (col0 + 32 * u < Lp) {  // warp-uniform
-            tmem_ld8(tc->tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(col0 + 32 * u), q[u]);
+            tmem_ld8(tc->tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(256 * ur + col0 + 32 * u), q[u]);
           } else {
 #pragma unroll
             for (int c = 0; c < 8; ++c) q[u][c] = 0.f;
@@ -520,6 +537,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
           }
           rf_st8(Gi + col0 + 32 * u, nv, vec, q[u]);
         }
+      }
       }
       tc_fence_before();
       __syncthreads();
