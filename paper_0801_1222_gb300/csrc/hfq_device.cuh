@@ -39,14 +39,14 @@ constexpr int kStatusTimeout = 4;    // a bounded wait gave up
 // ---------------------------------------------------------------------------
 constexpr int kRfBits = 7;        // bits per slice
 constexpr int kRfSlicesA = 6;     // slices of A (42 bits)
-constexpr int kRfSlicesH = 3;     // slices of H' (21 bits)
+constexpr int kRfSlicesH = 4;     // slices of H' (28 bits)
 constexpr int kRfLevels = 6;      // products p + q = 0 .. 5 kept, one FP32 accumulator per level
 constexpr int kRfNMax = 80;       // columns of G per product tile: 64 or 80 per grid (rc.nN)
 constexpr int kRfKC = 32;         // K (contraction) extent of one staged chunk of the residual product
 constexpr int kRf2KC = 64;        // the same for the update product
 constexpr int kRfTileA = 128 * kRfKC * 2;        // bytes of one A slice of a (row block, K chunk)
 constexpr int kRfTileH = kRfNMax * kRfKC * 2;    // bytes of one H' slice of a (column block, K chunk)
-constexpr int kRfStage = kRfSlicesA * kRfTileA + kRfSlicesH * kRfTileH;  // 63 KiB: one chunk
+constexpr int kRfStage = kRfSlicesA * kRfTileA + kRfSlicesH * kRfTileH;  // 68 KiB: one chunk
 constexpr int kRfSmem = 2 * kRfStage;            // two stage buffers
 
 struct RefineConst {

@@ -18,14 +18,11 @@
 // for FP16 tensor-core operands):
 //   * A (one table per grid, hfq_setup's k_refine_prep) = 2^ea sum_p a_p 2^{-7(p+1)},
 //     6 signed 7-bit slices; the field-dependent diagonal is patched in per chain;
-//   * H' = the FP32 H = fl32((1 + d_j) G_jn) rounded to the grid 2^{eh-21}
-//     (eh: |H| < 2^eh) = 2^eh sum_q h_q 2^{-7(q+1)}, 3 slices, cut straight
+//   * H' = the FP32 H = fl32((1 + d_j) G_jn) rounded to the grid 2^{eh-28}
+//     (eh: |H| < 2^eh) = 2^eh sum_q h_q 2^{-7(q+1)}, 4 slices, cut straight
 //     into shared memory chunk by chunk while A's slices arrive.  G' =
 //     (1 + D)^{-1} H' differs from G by at most half that grid step; E and
-//     the update both use this same G', so Newton's identity holds for it:
-//     only A must be exact, H' merely picks the starting point, and the
-//     rounding adds ~2^-21 |A||H| to E, far below the drift of 64 flips
-//     that one step removes (four slices gave the same refined G);
+//     the update both use this same G', so Newton's identity holds for it;
 //   * a_p, h_q are integers with |.| <= 128 (first slice) or <= 64, exact in
 //     FP16.  The products with p + q = l go to one FP32 TMEM accumulator per
 //     level l = 0..5 (at most four pairs, each K term <= 6 * 2^12 in all, so
@@ -220,9 +217,9 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
     }
     const float s7 = pow2f(kRfBits - eh);  // H 2^{7-eh}: below 2^7 in magnitude
 
-    // ---- GEMM1: E = 1 - A H', tile by tile (128 rows x nN columns) ---------
+    // ---- GEMM1: E = 1 - A H', tile by tile (128 rows x 64 columns) ---------
     // K goes in chunks of 32 through two stage buffers (A's six slices, 48
-    // KiB, by one bulk copy; H''s three, up to 15 KiB, cut by nN * 4 threads from G):
+    // KiB, by one bulk copy; H''s four, 16 KiB, cut by 256 threads from G):
     // chunk kc + 1 is brought in while the tensor cores multiply chunk kc.
     // Every commit of a chunk's MMAs is waited for exactly once, in order,
     // so each barrier's parity stays in step.
@@ -394,10 +391,8 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
     const int Lp = rf_pad(L, 16), nkc2 = rf_pad(L, kRf2KC) / kRf2KC;
     const uint32_t bl = (uint32_t)Lp * kRf2KC * 2u;  // bytes of one E^T part (hi or lo)
     constexpr uint32_t kAbuf = 2u * 128u * kRf2KC * 2u;  // one row block's H' hi and lo
-    constexpr int kHb = kRfBits * kRfSlicesH;       // bits of H' below 2^eh (21)
-    const float sH = pow2f(kHb - eh);               // H' = rint(H 2^{21-eh}) 2^{eh-21}
-    const float sE = pow2f(se), sHi = pow2f(eh - kHb), sQ = pow2f(eh - 14 - se);
-    const float s14 = pow2f(14 - kHb);              // rint(H 2^{21-eh}) 2^{-7} = H' 2^{14-eh}
+    const float sH = pow2f(28 - eh);                // H' = rint(H 2^{28-eh}) 2^{eh-28}
+    const float sE = pow2f(se), sHi = pow2f(eh - 28), sQ = pow2f(eh - 14 - se);
     // two row blocks of 128 and at most 256 columns: both blocks' products at
     // once (accumulators at TMEM columns 0 and 256), so each E^T chunk is
     // staged once; else one row block at a time
@@ -431,7 +426,7 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
             uint32_t h[4], l[4];
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
-              const float xa = rintf(x[u][t] * cp * sH) * s14, xb = rintf(x[u][t + 1] * cp * sH) * s14;
+              const float xa = rintf(x[u][t] * cp * sH) * 0x1p-14f, xb = rintf(x[u][t + 1] * cp * sH) * 0x1p-14f;
               h[t / 2] = f32x2_to_f16x2(xa, xb);
               l[t / 2] = f32x2_to_f16x2(xa - f16_lo_to_f32(h[t / 2]), xb - f16_hi_to_f32(h[t / 2]));
             }

@@ -6,8 +6,8 @@ equation built by the oracle.
 The steps restated, for one spin and field:
   * A = M^{-1} - diag(1 - e^{-sigma lambda s_j}), cut into six signed 7-bit
     slices under one scale 2^ea (rint of the running remainder times 2^7);
-  * H = fl32(fl32(e^{sigma lambda s_j}) G_jn) and H' = rint(H 2^{21-eh})
-    2^{eh-21}, which equals the sum of its three 7-bit slices;
+  * H = fl32(fl32(e^{sigma lambda s_j}) G_jn) and H' = rint(H 2^{28-eh})
+    2^{eh-28}, which equals the sum of its four 7-bit slices;
   * the products of slices p, q with p + q = l summed over the contraction
     index (a tensor core's FP32 accumulation: every partial sum an integer
     below 2^24 in magnitude), the six level sums combined as
@@ -19,7 +19,7 @@ lands on the FP64 inverse to within a few FP32 roundings."""
 import numpy as np
 import pytest
 
-BITS, SA, SH, LEVELS = 7, 6, 3, 6
+BITS, SA, SH, LEVELS = 7, 6, 4, 6
 
 
 def slices(x, scale_exp, n):
@@ -51,7 +51,7 @@ def refine_step(Minv, G32, s, lam, sig):
     H = (G32.astype(np.float32) * cplus[v][:, None].astype(np.float32)).astype(np.float64)
     eh = int(np.frexp(np.abs(H).max())[1])
     Hs = slices(H, eh, SH)
-    Hp = np.rint(np.ldexp(H, BITS * SH - eh)) * 2.0 ** (eh - BITS * SH)
+    Hp = np.rint(np.ldexp(H, 28 - eh)) * 2.0 ** (eh - 28)
     assert np.array_equal(sum(Hs[q] * 2.0 ** (eh - BITS * (q + 1)) for q in range(SH)), Hp)
     # level sums with every partial sum along the contraction index
     S = []
@@ -120,15 +120,15 @@ def test_partial_sum_bound_at_the_largest_slices():
 
 
 def test_h_prime_equals_its_slices_at_ties():
-    """rint(H 2^{21-eh}) 2^{eh-21} (the kernels' H' in the update) equals the
-    sum of the three slices (the residual's H'), ties included."""
+    """rint(H 2^{28-eh}) 2^{eh-28} (the kernels' H' in the update) equals the
+    sum of the four slices (the residual's H'), ties included."""
     rng = np.random.default_rng(5)
     eh = 5
     H = rng.uniform(-32, 32, 20000).astype(np.float32).astype(np.float64)
-    ties = (np.arange(-2000, 2000) + 0.5) * 2.0 ** (eh - BITS * SH)
+    ties = (np.arange(-2000, 2000) + 0.5) * 2.0 ** (eh - 28)
     H = np.concatenate([H, ties, ties * 3, [31.999999, -31.999999, 0.0]])
     Hs = slices(H, eh, SH)
-    direct = np.rint(np.ldexp(H, BITS * SH - eh)) * 2.0 ** (eh - BITS * SH)
+    direct = np.rint(np.ldexp(H, 28 - eh)) * 2.0 ** (eh - 28)
     assert np.array_equal(sum(Hs[q] * 2.0 ** (eh - BITS * (q + 1)) for q in range(SH)), direct)
     assert all(np.abs(Hs[0]).max() <= 128 and np.abs(Hs[q]).max() <= 64 for q in range(1, SH))
 
