@@ -39,16 +39,18 @@ def _chain_G(ctx, grid, chains, n_meas):
     return out
 
 
-def paired_run(beta, grids, chains, seed, n_warm, n_meas, **kw32):
+def paired_run(beta, grids, chains, seed, n_warm, n_meas, g0=None, **kw32):
     """FP32 delayed run that records its flips, FP64 rank-1 run that replays
-    them; per grid the paired statistics of G(tau) and D."""
+    them; per grid the paired statistics of G(tau) and D.  g0: the baths per
+    grid (the Bethe bath by default)."""
     from paper_0801_1222_gb300 import inputs
     h = lib()
     U = [g[0] for g in grids]
     dt = [g[1] for g in grids]
     Ls = [int(round(beta / d)) for d in dt]
     S = n_warm + n_meas
-    g0 = [inputs.bethe_G0_tau(beta, L) for L in Ls]
+    if g0 is None:
+        g0 = [inputs.bethe_G0_tau(beta, L) for L in Ls]
     ctx32 = h.HFQMC(beta, U, dt, [chains] * len(grids), seed=seed, precision="f32_delayed",
                     drift_fail=1.0, **kw32)
     for i, g in enumerate(g0):
@@ -178,3 +180,24 @@ def test_paired_G_tau_L200_L240_long_interval():
     for r in res:
         assert r["stats"]["k"] == 16 and r["stats"]["n_wrap"] == 16384
         _assert_within(r, 2)
+
+
+def test_paired_G_tau_on_a_self_consistent_insulating_bath():
+    """The criterion on a bath the DMFT loop produces, not the
+    non-interacting one: three iterations of the multigrid loop at U = 5.2,
+    beta = 40 (the insulating side of config 5) on Lambda = 120 and 200, then
+    the Lambda = 200 bath at the configurations' N_wrap = 64 with the
+    refinement, 32 chains, 320 sweeps."""
+    from paper_0801_1222_gb300 import dmft
+    h = lib()
+    beta, U = 40.0, 5.2
+    dtaus = [beta / 120, beta / 200]
+    ctx = h.HFQMC(beta, U, dtaus, [64, 64], seed=3, precision="f32_delayed", drift_fail=1.0)
+    loop = dmft.MultigridDMFT(ctx, beta, dtaus, n_fine=801, n_iw=2048, ph_symmetric=True)
+    for it in range(3):
+        loop.iterate(300 if it == 0 else 100, 300)
+    ctx.close()
+    g0 = loop.bath_on_grid(200)
+    r, = paired_run(beta, [(U, beta / 200)], 32, 17, 20, 300, g0=[g0], n_wrap=64)
+    assert r["stats"]["n_wrap"] == 64
+    _assert_within(r, 50)
