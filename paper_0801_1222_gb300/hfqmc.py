@@ -273,7 +273,12 @@ class _TorchAllocator:
 
 
 class HFQMC:
-    """One context: several (U, dtau) grids x chains, fixed beta."""
+    """One context: several (U, dtau) grids x chains, fixed beta.  The
+    keyword options map one to one onto hfqmc_opts (include/hfqmc.h); among
+    them recompute ("auto" = "refine" on the FP32 delayed path, "gj"),
+    refine_max (the Newton step's largest residual, 0 = 2^-8) and
+    ph_symmetry (0: with every grid's bath particle-hole symmetric the sweep
+    keeps G_up only; 1: only the recompute uses the symmetry; -1: never)."""
 
     def __init__(self, beta, U, dtau, chains_per_grid, seed=1, precision="f32_delayed", k=0,
                  n_wrap=0, accept_rule="metropolis", drift_fail=1e-1, flush="auto",
