@@ -3,8 +3,10 @@
 Workload (default "multigrid_L100_240"): Bethe lattice (W = 4) at half
 filling, U = 5, beta = 40, six dtau grids Lambda in {100,120,140,160,200,240},
 64 independent chains per grid, all 384 chains in one persistent launch,
-FP32 G with delayed rank-k updates (split-FP16 tensor-core flush) and periodic
-FP64 recomputation.  One step = one hfqmc_sweep call of --sweeps measured
+FP32 G with delayed rank-k updates (split-FP16 tensor-core flush), recomputed
+every N_wrap = 64 accepted flips by a Newton refinement on the tensor cores
+(FP64 Gauss-Jordan as its fallback); the bath is particle-hole symmetric, so
+the sweep keeps G_up only.  One step = one hfqmc_sweep call of --sweeps measured
 sweeps on every chain (1000 by default; the paper-shaped run is 10^3 warm-up
 + 10^4 measured sweeps = 11 such steps).  The metric is HS flip proposals per
 second: sum over chains of Lambda x sweeps, divided by device time.
@@ -13,7 +15,9 @@ Printed (one JSON line, rank 0): value (device-timed, inputs resident),
 e2e (same metric through the C ABI from pinned host buffers, G0 upload and
 G(tau) download in the timed region), roofline of the sweep kernel,
 cpu_baseline (the FP64 oracle on the host cores, bounded sample), the FP64
-rank-1 GPU path on the same workload, and the FP32-vs-FP64 G(tau) error of
+rank-1 GPU path on the same workload, the same FP32 workload with the
+Gauss-Jordan recompute and at the long recompute interval (8192 / 16384),
+and the FP32-vs-FP64 G(tau) error of
 the benched configuration (g_tau_err_vs_fp64: per grid, the FP32 run's flips
 replayed by the FP64 rank-1 path, chain-paired difference of the measured
 G(tau), outside the timed region).
