@@ -217,9 +217,9 @@ __device__ inline float refine_spin(const GridConst& gc, const RefineConst& rc, 
     }
     const float s7 = pow2f(kRfBits - eh);  // H 2^{7-eh}: below 2^7 in magnitude
 
-    // ---- GEMM1: E = 1 - A H', tile by tile (128 rows x 64 columns) ---------
+    // ---- GEMM1: E = 1 - A H', tile by tile (128 rows x nN columns) ---------
     // K goes in chunks of 32 through two stage buffers (A's six slices, 48
-    // KiB, by one bulk copy; H''s four, 16 KiB, cut by 256 threads from G):
+    // KiB, by one bulk copy; H''s four, up to 20 KiB, cut by nN * 4 threads from G):
     // chunk kc + 1 is brought in while the tensor cores multiply chunk kc.
     // Every commit of a chunk's MMAs is waited for exactly once, in order,
     // so each barrier's parity stays in step.
