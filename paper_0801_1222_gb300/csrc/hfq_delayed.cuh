@@ -63,6 +63,14 @@ __host__ __device__ inline int del_spin_stride(int L, int KP) {
   return L * KP + ((16 - (L * KP) % 32) + 32) % 32;
 }
 
+// Floats of one panel (U or W): both spins at the padded stride, or, when the
+// sweep keeps G_up only (ns = 1), one spin plus 16 floats (the G_up-only sweep
+// starts W 16 floats into its region, off U's bank alignment).  A multiple of
+// 4 (KP is), so the panels are zeroed by 16-byte stores.
+__host__ __device__ inline int del_panel_floats(int L, int KP, int ns) {
+  return ns == 1 ? L * KP + 16 : del_spin_stride(L, KP) + L * KP;
+}
+
 // stage: W hi, W lo (one block of 128 rows), then U hi, U lo for ub U blocks
 // (at most kUBlk and at most as many as L has), FP16 in core-matrix layout,
 // 128 x KS each
@@ -83,8 +91,11 @@ __host__ __device__ inline size_t rf_smem_need(int L) {
   return g2 > (size_t)kRfSmem ? g2 : (size_t)kRfSmem;
 }
 
+// ns: spins the sweep keeps (2, or 1 for the G_up-only sweep): the panels and
+// the measurement's partial sums are sized for them; a resident G keeps both.
 __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, bool gj_smem,
-                                                bool gtile = false, int ub = kUBlk, bool refine = false) {
+                                                bool gtile = false, int ub = kUBlk, bool refine = false,
+                                                int ns = 2) {
   DelLayout d;
   d.ldS = L | 1;
   d.KP = K + 4;  // 16-byte rows; (K+4) mod 32 spreads 8 rows of a 16-byte load over all banks
@@ -108,7 +119,7 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   }
   // the staging area doubles as the measurement's per-warp partial sums and
   // holds the recompute's scratch when that is not in the head
-  const size_t part = 2 * (size_t)(kDelNT / 32) * L * 4;
+  const size_t part = (size_t)ns * (kDelNT / 32) * L * 4;
   const size_t scratch = del_align((size_t)L * 8, 128) + del_align((size_t)L * 4, 128);
   size_t st = del_stage_bytes(K, L, ub);
   if (part > st) st = part;
@@ -117,9 +128,9 @@ __host__ __device__ inline DelLayout del_layout(int L, int K, bool resident, boo
   d.off_G = o;
   if (resident) o += del_align(2 * (size_t)L * d.ldS * 4, 128);
   d.off_U = o;
-  o += del_align((size_t)(del_spin_stride(L, d.KP) + L * d.KP) * 4, 128);
+  o += del_align((size_t)del_panel_floats(L, d.KP, ns) * 4, 128);
   d.off_W = o;
-  o += del_align((size_t)(del_spin_stride(L, d.KP) + L * d.KP) * 4, 128);
+  o += del_align((size_t)del_panel_floats(L, d.KP, ns) * 4, 128);
   d.off_diag = o;
   o += del_align(2 * (size_t)L * 4, 128);
   d.off_gtile = 0;
@@ -791,14 +802,14 @@ __device__ __forceinline__ void measure_rows_reg(const float* Gu, const float* G
 //  * the plain row walk beyond.
 // Everything stays on the FP32 pipe: the caller folds the per-sweep totals
 // into FP64 accumulators.
-// part: 2 * NW * L floats of shared scratch; out[k], out[L+k] receive the
+// part: NSP * NW * L floats of shared scratch; out[k], out[L+k] receive the
 // sums (not yet divided by L).  NSP = 1: spin up only (out[k]).
 template <int NSP = 2>
 __device__ inline void measure_rows(const float* Gu, const float* Gd, int ld, int L, float* part,
                                     float* out) {
   constexpr int NW = kDelNT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < 2 * NW * L; e += kDelNT) part[e] = 0.f;
+  for (int e = threadIdx.x; e < NSP * NW * L; e += kDelNT) part[e] = 0.f;
   __syncthreads();
   if (L <= 256 && L % 4 == 0 && ld % 4 == 0 &&
       ((reinterpret_cast<uintptr_t>(Gu) | reinterpret_cast<uintptr_t>(Gd)) & 15) == 0) {

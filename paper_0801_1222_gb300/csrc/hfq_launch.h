@@ -31,8 +31,10 @@ int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cuda
 // delayed rank-k sweep (FP32); kDelayedTile: edge of the flush's output tiles
 // (the TMA reduce moves half a tile, kDelayedTile x kDelayedTile/2, at a time)
 constexpr int kDelayedTile = 128;
+// ns: spins the sweep keeps (1 for the G_up-only sweep of a particle-hole
+// symmetric bath)
 size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile = false, int ub = 2,
-                    bool refine = false);
+                    bool refine = false, int ns = 2);
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm);
 int launch_sweep_delayed(const SweepArgs& a, int ctas, size_t smem, cudaStream_t st);
 

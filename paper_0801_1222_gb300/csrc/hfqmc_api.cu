@@ -34,6 +34,8 @@ thread_local std::string g_create_error;
 struct GridHost {
   double U, dtau, lambda;
   int L, chains, item0, k, n_wrap, resident, gj_smem, gtile = 0, ub = 2;
+  int k_req = 0;        // the delay depth asked for (option or table), before fitting
+  int k1 = 0, ub1 = 2;  // k and U blocks of the G_up-only sweep's layout (one spin's panels)
   bool refine = false;  // recompute by Newton refinement (FP32 delayed path)
   uint16_t* d_aslc = nullptr;  // its slice table of A (device)
   bool g0_set = false, ever_set = false;
@@ -122,6 +124,7 @@ struct hfqmc_ctx {
   // sweep launch shape
   size_t sweep_smem = 0;
   int sweep_ctas = 0;
+  int layout_ns = 2;  // spins the current shared-memory layout (gc[].k, ub, sweep_smem) is fitted for
   // instantiated graphs of hfqmc_sweep per (n_warm, n_meas), with the call
   // stamp of their last use (at most kMaxGraphs kept; the least recently used
   // one is destroyed first)
@@ -202,6 +205,16 @@ static int sweep_mirrors(const hfqmc_ctx* c) {
   return 1;
 }
 
+// The sweep launch runs the refining kernel when some grid refines with
+// lambda != 0, and its G_up-only variant only then (a context whose grids
+// all have lambda = 0 runs the plain two-spin kernel).
+static int launch_refines(const hfqmc_ctx* c) {
+  for (int g = 0; g < c->n_grids; ++g)
+    if (c->gh[g].refine && c->gh[g].lambda != 0.0) return 1;
+  return 0;
+}
+static int launch_mirrors(const hfqmc_ctx* c) { return launch_refines(c) ? sweep_mirrors(c) : 0; }
+
 void drop_graphs(hfqmc_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
@@ -224,12 +237,8 @@ int launch_sweep_kernel(hfqmc_ctx* c, long long n_warm, long long n_meas) {
   a.accept_rule = c->opts.accept_rule;
   a.flush = c->opts.flush;
   a.trace_mode = c->trace_mode;
-  a.refine = 0;
-  for (int g = 0; g < c->n_grids; ++g)
-    if (c->gh[g].refine && c->gh[g].lambda != 0.0) a.refine = 1;
-  // the G_up-only variant exists for the refining kernel only (a context
-  // whose grids all have lambda = 0 runs the plain two-spin kernel)
-  a.mirror = a.refine ? sweep_mirrors(c) : 0;
+  a.refine = launch_refines(c);
+  a.mirror = launch_mirrors(c);
   if (c->opts.precision == HFQMC_F32_DELAYED)
     return launch_sweep_delayed(a, c->sweep_ctas, c->sweep_smem, c->stream);
   return launch_sweep_rank1(f64_path(c), a, c->sweep_ctas, c->sweep_smem, c->stream);
@@ -369,6 +378,7 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
         nw_t = (o.precision == HFQMC_F64_RANK1 || h.L > 128) ? 16384 : 8192;
     }
     h.k = (o.precision == HFQMC_F32_DELAYED) ? (o.k ? o.k : k_t) : 1;
+    h.k_req = h.k;
     h.n_wrap = o.n_wrap ? o.n_wrap : nw_t;
     size_t sm;
     // the FP64 recompute works in shared memory when its workspace fits next to the head;
@@ -578,6 +588,21 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
     c->gc[g].gtile = h.gtile;
     c->gc[g].tmapG = h.gtile ? (const void*)(c->d_tmaps + g) : nullptr;
   }
+  // the G_up-only sweep's layout: one spin's panels and partial sums leave
+  // room for a deeper delay (up to the k asked for) on grids whose G stays in
+  // HBM; residency and the flush kind stay those of the two-spin layout
+  for (int g = 0; g < n_grids; ++g) {
+    GridHost& h = c->gh[g];
+    h.k1 = h.k;
+    h.ub1 = h.ub;
+    if (o.precision != HFQMC_F32_DELAYED || h.resident) continue;
+    for (int kt = h.k_req; kt > h.k && h.k1 == h.k; kt -= 8)
+      for (int ub = 2; ub >= 1 && h.k1 == h.k; --ub)
+        if (delayed_smem(h.L, kt, false, h.gj_smem, h.gtile != 0, ub, h.refine, 1) <= kSmemMax) {
+          h.k1 = kt;
+          h.ub1 = ub;
+        }
+  }
   if ((e = cudaMemcpyAsync(c->d_tmaps, tmaps.data(), sizeof(CUtensorMap) * n_grids, cudaMemcpyHostToDevice,
                            c->stream)) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaMemcpyAsync"));
@@ -635,6 +660,34 @@ int create_impl(hfqmc_ctx** out, double beta, const double* U, bool per_grid_U,
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamSynchronize(create)"));
   *out = c;
+  return HFQMC_OK;
+}
+
+// Fits every grid's k and U blocks, and the sweep's shared memory, to the
+// layout of the delayed kernel variant about to run (ns = 1: the G_up-only
+// sweep, ns = 2: both spins), uploads the grids' constants and drops the
+// cached graphs (their launches carry the old size).  Runs on the host before
+// a sweep whose variant differs from the last one; a chain's panels are empty
+// between calls, so its delay depth may change there.
+int apply_layout(hfqmc_ctx* c, int ns) {
+  size_t sm = 0;
+  for (int g = 0; g < c->n_grids; ++g) {
+    const GridHost& h = c->gh[g];
+    GridConst& q = c->gc[g];
+    q.k = ns == 1 ? h.k1 : h.k;
+    q.ub = ns == 1 ? h.ub1 : h.ub;
+    sm = std::max(sm, delayed_smem(h.L, q.k, h.resident != 0, h.gj_smem != 0, h.gtile != 0, q.ub, h.refine, ns));
+  }
+  int threads = 0, occ = 0;
+  const int r = delayed_config(sm, &threads, &occ);
+  if (r) return cuda_fail(c, (cudaError_t)r, "sweep kernel configuration");
+  if (occ < 1) return fail(c, HFQMC_EINVAL, "sweep kernel does not fit on an SM");
+  CK(cudaMemcpyAsync(c->d_grids, c->gc.data(), sizeof(GridConst) * c->n_grids, cudaMemcpyHostToDevice,
+                     c->stream));
+  c->sweep_smem = sm;
+  c->sweep_ctas = std::min(c->n_items, occ * c->n_sm);
+  drop_graphs(c);
+  c->layout_ns = ns;
   return HFQMC_OK;
 }
 
@@ -744,6 +797,13 @@ int hfqmc_sweep(hfqmc_ctx* c, int64_t n_warm, int64_t n_meas) {
       return fail(c, HFQMC_ESTATE, "hfqmc_set_G0 has not been called for grid " + std::to_string(g));
   if (c->trace_mode != kTraceOff && n_warm + n_meas > c->trace_cap)
     return fail(c, HFQMC_EINVAL, "more sweeps than the decision trace holds (hfqmc_set_trace)");
+  if (c->opts.precision == HFQMC_F32_DELAYED) {
+    const int ns = launch_mirrors(c) ? 1 : 2;
+    if (ns != c->layout_ns) {
+      const int r = apply_layout(c, ns);
+      if (r) return r;
+    }
+  }
   CK(cudaEventRecord(c->ev0, c->stream));
   if (c->opts.use_graph) {
     auto key = std::make_pair((long long)n_warm, (long long)n_meas);
@@ -828,7 +888,7 @@ int hfqmc_get_stats(hfqmc_ctx* c, int grid, hfqmc_stats* out) {
   const GridHost& h = c->gh[grid];
   out->L = h.L;
   out->chains = h.chains;
-  out->k = h.k;
+  out->k = c->gc[grid].k;  // the layout of the last sweep's kernel variant
   out->n_wrap = h.n_wrap;
   out->sweeps = c->sweeps_done;
   out->proposals = o.proposals;

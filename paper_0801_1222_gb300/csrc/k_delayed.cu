@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     const GridConst gc = a.grids[ip.grid];
     const int L = gc.L, K = gc.k;
     const bool resident = gc.resident != 0;
-    const DelLayout lay = del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0, gc.ub, gc.rc != nullptr);
+    const DelLayout lay =
+        del_layout(L, K, resident, gc.gj_smem != 0, gc.gtile != 0, gc.ub, gc.rc != nullptr, kMirror ? 1 : 2);
     // product tile buffer of the TMA reduce flush (G in HBM, tensor map set)
     float* dtile = gc.gtile ? reinterpret_cast<float*>(smem + lay.off_gtile) : nullptr;
 
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     int8_t* ss = reinterpret_cast<int8_t*>(smem + lay.off_s);
     unsigned char* stage = smem + lay.off_stage;
     const int KP = lay.KP;
-    const int panel_floats4 = (del_spin_stride(L, KP) + L * KP) / 4;  // one panel, both spins
+    const int panel_floats4 = del_panel_floats(L, KP, kMirror ? 1 : 2) / 4;  // one panel, the kept spins
     auto zero_panels = [&]() {
       for (int e = tid; e < 2 * panel_floats4; e += NT)
         reinterpret_cast<float4*>(e < panel_floats4 ? Pu : Pw)[e < panel_floats4 ? e : e - panel_floats4] =
@@ -127,9 +128,9 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
     int sv[kRowsPerThread];
     bool lastbad[kRowsPerThread];
     float* Gs = (sp && !kMirror) ? Gd : Gu;
-    // G_up only: W starts 16 floats past the panel block (inside the unused
-    // second spin's space), so row r of U and row r of W lie in different
-    // shared-memory banks (see the append)
+    // G_up only: W starts 16 floats into its region (sized one spin plus 16
+    // floats), so row r of U and row r of W lie in different shared-memory
+    // banks (see the append)
     float* const Pw1 = kMirror ? Pw + 16 : Pw;
     float* Us = Pu + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
     float* Ws = Pw1 + (size_t)(kMirror ? 0 : sp) * del_spin_stride(L, KP);
@@ -509,8 +510,8 @@ __global__ void __launch_bounds__(kDelNT, 1) k_sweep_delayed(SweepArgs a) {
   if (use_tc) tc_teardown(&tc);
 }
 
-size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int ub, bool refine) {
-  return del_layout(L, k, resident, gj_smem, gtile, ub, refine).bytes;
+size_t delayed_smem(int L, int k, bool resident, bool gj_smem, bool gtile, int ub, bool refine, int ns) {
+  return del_layout(L, k, resident, gj_smem, gtile, ub, refine, ns).bytes;
 }
 
 int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {

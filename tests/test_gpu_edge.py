@@ -1,7 +1,8 @@
 """Edge cases of the sweep through the C ABI: the smallest grids (Lambda = 1,
 2, 3), the largest the delayed path takes (Lambda = 512, more rows than
 threads), the large-Lambda workload shape (Lambda = 500, where k is lowered
-to fit the panels on chip), and the size limits."""
+to fit the panels on chip: to 8 with both spins' panels, to 24 when the
+sweep keeps G_up only), and the size limits."""
 import numpy as np
 import pytest
 
@@ -53,10 +54,37 @@ def test_lambda_512_delayed_follows_oracle(orc):
     assert same >= 2
 
 
+@pytest.mark.parametrize("beta,U,dtau,k,k_fit", [(50.0, 4.8, 0.1, 64, 24), (40.0, 5.0, 0.125, 40, 40)])
+def test_one_spin_layout_deeper_delay_follows_oracle(orc, beta, U, dtau, k, k_fit):
+    """The particle-hole symmetric bath runs the G_up-only sweep, whose panels
+    hold one spin: at Lambda = 500 the requested k = 64 is lowered to 24
+    (8 with both spins' panels), at Lambda = 320 k = 40 fits (16 with both).
+    With the recompute every 64 accepted flips, most chains follow the
+    oracle's decisions over a sweep, and those that do hold both spins' G
+    within the FP32 drift (at least two must)."""
+    ctx, q = make_pair(orc, beta, [(U, dtau)], [4], precision="f32_delayed", k=k, n_wrap=64,
+                       drift_fail=1.0)
+    ctx.sweep(0, 1)
+    q.sweep(0, 1)
+    st = ctx.get_stats(0)
+    assert st["ph_symmetric"] == 1 and st["k"] == k_fit, st
+    assert st["recomputes"] >= 4 and st["recompute_fallbacks"] == 0
+    same = 0
+    for c, och in enumerate(q.chains[0]):
+        gc = ctx.get_chain(0, c)
+        assert gc["accepted"] > 64
+        if gc["hash"] == och.decision_hash:
+            same += 1
+            err = max(np.abs(gc["Gup"] - och.Gup).max(), np.abs(gc["Gdn"] - och.Gdn).max())
+            assert err < 1e-3
+    assert same >= 2
+
+
 def test_large_lambda_workload_shape_runs():
     """Lambda = 500 (U = 4.8, beta = 50): the requested k = 64 does not fit the
-    panels of both spins on chip, so the library lowers it; FP32 G(tau)
-    follows the FP64 path on the same chains over a short run."""
+    panels on chip, so the library lowers it (to 24 for the G_up-only sweep
+    of this particle-hole symmetric bath); FP32 G(tau) follows the FP64 path
+    on the same chains over a short run."""
     from paper_0801_1222_gb300 import inputs
     h = lib()
     beta, U, L = 50.0, 4.8, 500
@@ -71,7 +99,7 @@ def test_large_lambda_workload_shape_runs():
         ctx.close()
     (G64, _), _ = res["f64_rank1"]
     (G32, _), st = res["f32_delayed"]
-    assert st["k"] <= 64 and st["recomputes"] > 0 and st["drift_max"] < 1.0
+    assert st["k"] == 24 and st["recomputes"] > 0 and st["drift_max"] < 1.0
     assert np.max(np.abs(G32 - G64)) < 5e-3
 
 
