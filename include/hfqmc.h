@@ -73,7 +73,11 @@ typedef void (*hfqmc_free_fn)(void *ptr, void *user);
 
 typedef struct {
     int precision;      /* HFQMC_F64_RANK1 | HFQMC_F32_RANK1 | HFQMC_F32_DELAYED    */
-    int k;              /* delay depth for F32_DELAYED (8..64, multiple of 8); 0 = per-Lambda table */
+    int k;              /* delay depth for F32_DELAYED (8..64, multiple of 8); 0 = per-Lambda table.
+                           Lowered in steps of 8 where the panels do not fit in shared memory:
+                           the two-spin sweep holds both spins' panels, the G_up-only sweep of a
+                           particle-hole symmetric bath one spin's (Lambda = 500: k <= 8 and
+                           <= 24); hfqmc_stats.k reports the value the last sweep ran with */
     int n_wrap;         /* FP64 recompute every n_wrap accepted flips; <0 = never; 0 = per-Lambda table
                            (F32_DELAYED: 64, the multigrid configuration's interval; rank-1 paths
                            without a tune_table: 16384 for F64_RANK1, 8192 / 16384 (Lambda > 128)
@@ -134,7 +138,8 @@ enum { HFQMC_RECOMPUTE_AUTO = 0, HFQMC_RECOMPUTE_GJ = 1, HFQMC_RECOMPUTE_REFINE 
 typedef struct {
     int L;                  /* Lambda = beta/dtau */
     int chains;
-    int k;                  /* delay depth in use (1 for rank-1 paths) */
+    int k;                  /* delay depth of the last sweep's layout (before any sweep: the
+                               two-spin one; 1 for rank-1 paths) */
     int n_wrap;             /* recompute interval in use */
     int64_t sweeps;         /* sweeps done per chain since the first set_G0 */
     int64_t proposals;      /* summed over chains */

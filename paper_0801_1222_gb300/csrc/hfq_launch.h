@@ -7,6 +7,20 @@
 
 namespace hfq {
 
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least smem bytes and never lowers it: the limit belongs to the function,
+// while every context of the process launches the same sweep kernels with its
+// own size, set once and launched later (a lower size set by one context
+// would make another's launches fail).
+template <typename F>
+inline cudaError_t raise_smem_limit(F* f, size_t smem) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
+  if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
 // bath matrix M of one grid from G0(tau_k), and its FP64 inverse
 int launch_bath_matrix(int L, const double* G0_tau, double* M, cudaStream_t st);
 int launch_bath_inverse(int L, const double* M, double* Minv, int* status, cudaStream_t st);

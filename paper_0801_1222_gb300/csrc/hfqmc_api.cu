@@ -673,15 +673,18 @@ int apply_layout(hfqmc_ctx* c, int ns) {
   size_t sm = 0;
   for (int g = 0; g < c->n_grids; ++g) {
     const GridHost& h = c->gh[g];
-    GridConst& q = c->gc[g];
-    q.k = ns == 1 ? h.k1 : h.k;
-    q.ub = ns == 1 ? h.ub1 : h.ub;
-    sm = std::max(sm, delayed_smem(h.L, q.k, h.resident != 0, h.gj_smem != 0, h.gtile != 0, q.ub, h.refine, ns));
+    sm = std::max(sm, delayed_smem(h.L, ns == 1 ? h.k1 : h.k, h.resident != 0, h.gj_smem != 0, h.gtile != 0,
+                                   ns == 1 ? h.ub1 : h.ub, h.refine, ns));
   }
   int threads = 0, occ = 0;
   const int r = delayed_config(sm, &threads, &occ);
   if (r) return cuda_fail(c, (cudaError_t)r, "sweep kernel configuration");
   if (occ < 1) return fail(c, HFQMC_EINVAL, "sweep kernel does not fit on an SM");
+  // the grids' constants change only once the new size is in place
+  for (int g = 0; g < c->n_grids; ++g) {
+    c->gc[g].k = ns == 1 ? c->gh[g].k1 : c->gh[g].k;
+    c->gc[g].ub = ns == 1 ? c->gh[g].ub1 : c->gh[g].ub;
+  }
   CK(cudaMemcpyAsync(c->d_grids, c->gc.data(), sizeof(GridConst) * c->n_grids, cudaMemcpyHostToDevice,
                      c->stream));
   c->sweep_smem = sm;

@@ -518,7 +518,7 @@ int delayed_config(size_t smem, int* threads, int* ctas_per_sm) {
   cudaError_t e = cudaSuccess;
   for (auto* f : {k_sweep_delayed<false, false>, k_sweep_delayed<true, false>, k_sweep_delayed<false, true>,
                   k_sweep_delayed<true, true>, k_sweep_delayed<false, true, true>, k_sweep_delayed<true, true, true>})
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = raise_smem_limit(f, smem);
   int occ = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_delayed<false, true>, kDelNT, smem);

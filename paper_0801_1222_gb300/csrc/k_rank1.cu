@@ -364,14 +364,9 @@ int launch_sweep_rank1(bool f64, const SweepArgs& a, int ctas, size_t smem, cuda
 
 template <typename T>
 static cudaError_t config_rank1_t(size_t smem, int* occ) {
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_rank1<T, kTraceOff>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sweep_rank1<T, kTraceRecord>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sweep_rank1<T, kTraceReplay>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+  cudaError_t e = raise_smem_limit(k_sweep_rank1<T, kTraceOff>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_sweep_rank1<T, kTraceRecord>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_sweep_rank1<T, kTraceReplay>, smem);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_sweep_rank1<T, kTraceOff>, R1Traits<T>::NT,
                                                       smem);

@@ -209,3 +209,30 @@ def test_tma_reduce_flush_matches_register_flush():
         assert a["accepted"] == b["accepted"] and a["accepted"] > 0
         np.testing.assert_array_equal(a["Gup"], b["Gup"])
         np.testing.assert_array_equal(a["Gdn"], b["Gdn"])
+
+
+def test_live_contexts_with_different_shared_memory_sizes():
+    """Contexts of one process share the sweep kernels, whose dynamic
+    shared-memory limit the library raises and never lowers: a context
+    whose layout needs the most shared memory (Lambda = 240, both spins kept:
+    an asymmetric bath setting) still launches after smaller ones were created
+    and have swept, among them one switched to the G_up-only layout."""
+    from paper_0801_1222_gb300 import inputs
+    h = lib()
+    big = h.HFQMC(40.0, 5.0, [40.0 / 240], [2], seed=5, precision="f32_delayed", n_wrap=64, drift_fail=1.0,
+                  ph_symmetry=-1)
+    big.set_G0(0, inputs.bethe_G0_tau(40.0, 240))
+    small = h.HFQMC(8.0, 4.0, [0.2], [2], seed=5, precision="f32_delayed", n_wrap=64, drift_fail=1.0)
+    small.set_G0(0, inputs.bethe_G0_tau(8.0, 40))
+    mid = h.HFQMC(40.0, 5.0, [40.0 / 200], [2], seed=5, precision="f32_delayed", n_wrap=64, drift_fail=1.0)
+    mid.set_G0(0, inputs.bethe_G0_tau(40.0, 200))
+    try:
+        for ctx in (small, mid, big, small, mid, big):
+            ctx.sweep(0, 2)
+        for ctx, ph in ((big, 0), (small, 1), (mid, 1)):
+            st = ctx.get_stats(0)
+            assert st["accepted"] > 0 and st["ph_symmetric"] == ph
+            assert np.all(np.isfinite(ctx.get_G(0)[0]))
+    finally:
+        for ctx in (big, small, mid):
+            ctx.close()
