@@ -46,7 +46,7 @@ LONG_NWRAP_TABLE = [(64, 32, 8192), (128, 32, 8192), (144, 32, 16384), (176, 24,
 # dram read + write of one full-size launch (1000 sweeps of the multigrid
 # workload at N_wrap 64), from a one-pass ncu capture of this kernel (None
 # while the kernel has changed since)
-TRAFFIC_PER_1000_SWEEPS = 345468416 + 22745530624
+TRAFFIC_PER_1000_SWEEPS = 338328576 + 23488740096
 
 
 def parse():
