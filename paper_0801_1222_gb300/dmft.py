@@ -30,10 +30,27 @@ def matsubara(beta: float, n_iw: int) -> np.ndarray:
     return (2 * np.arange(n_iw) + 1) * np.pi / float(beta)
 
 
+def _uniform_steps(beta, tau):
+    """M when tau_k = k beta / M for k = 0..len(tau)-1 (len(tau) <= M + 1), else 0."""
+    if tau.shape[0] < 2 or tau[0] != 0.0:
+        return 0
+    M = int(round(beta / (tau[1] - tau[0])))
+    if M < 1 or tau.shape[0] > M + 1:
+        return 0
+    dev = np.max(np.abs(tau - np.arange(tau.shape[0]) * (beta / M)))
+    return M if dev <= 1e-12 * beta else 0
+
+
 def spline_ft(beta, tau, G, n_iw):
-    """G(iw_n), n = 0..n_iw-1, from G on the uniform grid tau[0] = 0+ .. tau[-1] = beta-."""
+    """G(iw_n), n = 0..n_iw-1, from G on the uniform grid tau[0] = 0+ .. tau[-1] = beta-.
+
+    The piecewise-constant third derivative s3_k on interval k enters as
+    sum_k e^{iw_n tau_k} s3_k; with tau_k = k h, h = beta / N, the phase is
+    e^{i pi k / N} e^{2 pi i n k / N}, so the sum over k is one inverse DFT of
+    length N of s3_k e^{i pi k / N}, read at n mod N."""
     tau = np.asarray(tau, dtype=np.float64)
     G = np.asarray(G, dtype=np.float64)
+    N = tau.shape[0] - 1
     h = tau[1] - tau[0]
     sp = CubicSpline(tau, G, bc_type="not-a-knot")
     d1, d2, d3 = sp.derivative(1), sp.derivative(2), sp.derivative(3)
@@ -42,21 +59,36 @@ def spline_ft(beta, tau, G, n_iw):
     S0, Sb = G[0], G[-1]
     out = (-(Sb + S0) / iw + (d1(tau[-1]) + d1(tau[0])) / iw ** 2
            - (d2(tau[-1]) + d2(tau[0])) / iw ** 3)
-    ph = np.exp(np.outer(iw, tau[:-1]))          # n_iw x N
-    out -= (np.exp(iw * h) - 1.0) / iw ** 4 * (ph @ s3)
+    k = np.arange(N)
+    q = s3 * np.exp(1j * np.pi * k / N)
+    phs3 = N * np.fft.ifft(q)[np.arange(n_iw) % N]   # sum_k e^{iw_n tau_k} s3_k
+    out -= (np.exp(iw * h) - 1.0) / iw ** 4 * phs3
     return out
 
 
 def bath_tau(beta, tau, G0_iw):
-    """G0(tau) at the given tau values from its Matsubara values."""
+    """G0(tau) at the given tau values from its Matsubara values.
+
+    The sum over n of Re[e^{-iw_n tau} r_n] (r_n the Matsubara values less the
+    1/(iw) and 1/(iw)^3 tails) on a uniform grid tau_k = k beta / M: the phase
+    is e^{-i pi k / M} e^{-2 pi i n k / M}, so folding r_n onto n mod M turns
+    the sum into one DFT of length M; other tau are summed directly."""
     tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
     wn = matsubara(beta, G0_iw.shape[0])
     iw = 1j * wn
     rest = G0_iw - 1.0 / iw - 1.0 / iw ** 3
-    out = np.empty(tau.shape[0])
-    for a in range(0, tau.shape[0], 64):
-        t = tau[a:a + 64, None]
-        out[a:a + 64] = (2.0 / beta) * np.real(np.exp(-1j * wn[None, :] * t) * rest[None, :]).sum(axis=1)
+    M = _uniform_steps(float(beta), tau)
+    if M:
+        folded = np.bincount(np.arange(rest.shape[0]) % M, weights=rest.real, minlength=M) \
+            + 1j * np.bincount(np.arange(rest.shape[0]) % M, weights=rest.imag, minlength=M)
+        F = np.fft.fft(folded)
+        k = np.arange(tau.shape[0])
+        out = (2.0 / beta) * np.real(np.exp(-1j * np.pi * k / M) * F[k % M])
+    else:
+        out = np.empty(tau.shape[0])
+        for a in range(0, tau.shape[0], 64):
+            t = tau[a:a + 64, None]
+            out[a:a + 64] = (2.0 / beta) * np.real(np.exp(-1j * wn[None, :] * t) * rest[None, :]).sum(axis=1)
     out += -0.5 + tau * (beta - tau) / 4.0
     out[tau == 0.0] = -0.5
     out[tau == beta] = -0.5

@@ -27,15 +27,19 @@ def grid_taus(beta: float, L: int) -> np.ndarray:
     return np.arange(L + 1) * (float(beta) / L)
 
 
-def interpolate_to_fine(beta, G_grid, tau_fine, ref=None):
+def interpolate_to_fine(beta, G_grid, tau_fine, ref=None, ref_fine=None):
     """G_grid: the Lambda+1 values G(tau_k), k = 0..Lambda, of one grid.
-    ref: callable ref(tau) -> array, or None (no reference)."""
+    ref: callable ref(tau) -> array, or None (no reference); ref_fine: ref at
+    tau_fine when the caller has it already."""
     G_grid = np.asarray(G_grid, dtype=np.float64)
     L = G_grid.shape[0] - 1
     tk = grid_taus(beta, L)
     r_k = ref(tk) if ref is not None else 0.0
     spline = CubicSpline(tk, G_grid - r_k, bc_type="natural")
-    r_f = ref(tau_fine) if ref is not None else 0.0
+    if ref is None:
+        r_f = 0.0
+    else:
+        r_f = ref_fine if ref_fine is not None else ref(tau_fine)
     return spline(tau_fine) + r_f
 
 
@@ -74,7 +78,8 @@ def extrapolate(dtaus, G_fine, err_fine=None):
 def multigrid_estimate(beta, dtaus, G_list, err_list, tau_fine, ref=None):
     """The dtau -> 0 estimate on tau_fine from the per-grid G(tau_k) (each of
     length Lambda_i + 1) and their error bars (interpolated the same way)."""
-    Gf = np.array([interpolate_to_fine(beta, G, tau_fine, ref) for G in G_list])
+    ref_fine = ref(tau_fine) if ref is not None else None  # the same for every grid
+    Gf = np.array([interpolate_to_fine(beta, G, tau_fine, ref, ref_fine) for G in G_list])
     Ef = None
     if err_list is not None:
         Ef = np.array([np.abs(interpolate_to_fine(beta, E, tau_fine, None)) for E in err_list])

@@ -26,6 +26,48 @@ def test_bath_tau_round_trip():
     assert np.max(np.abs(dmft.bath_tau(beta, tau, G0_iw) - inputs.bethe_G0_at(beta, tau))) < 1e-9
 
 
+@pytest.mark.parametrize("M,K", [(80, 80), (320, 320), (1000, 1001), (240, 241), (7, 8)])
+def test_bath_tau_on_a_uniform_grid_by_dft_equals_the_direct_sum(M, K):
+    """On tau_k = k beta / M the Matsubara sum is taken as one DFT of the
+    frequencies folded onto n mod M; in any other order of the same points it
+    is summed term by term.  Both agree (a bath with noise in every
+    frequency, more frequencies than points and fewer)."""
+    beta = 40.0
+    rng = np.random.default_rng(3)
+    for n_iw in (4096, 5):
+        iw = 1j * dmft.matsubara(beta, n_iw)
+        G0_iw = inputs.bethe_G0_iw(iw) + 1e-3 * (rng.standard_normal(n_iw) + 1j * rng.standard_normal(n_iw)) / (1 + iw.imag ** 2)
+        tau = np.arange(K) * (beta / M)
+        fast = dmft.bath_tau(beta, tau, G0_iw)
+        direct = dmft.bath_tau(beta, tau[::-1], G0_iw)[::-1]  # not ascending from 0: summed directly
+        # the direct sum's phases w_n tau reach 2 pi n_iw: its own rounding is ~1e-13
+        assert np.max(np.abs(fast - direct)) < 1e-12
+
+
+def test_spline_ft_third_derivative_sum_by_dft():
+    """The sum over intervals of e^{iw_n tau_k} s3_k taken by one inverse DFT
+    equals the explicit phase matrix, for more frequencies than intervals and
+    fewer."""
+    from scipy.interpolate import CubicSpline
+    beta = 10.0
+    rng = np.random.default_rng(5)
+    for N, n_iw in ((100, 4096), (1000, 64)):
+        tau = np.linspace(0.0, beta, N + 1)
+        g = inputs.bethe_G0_at(beta, tau, 1 << 12) + 1e-3 * rng.standard_normal(N + 1)
+        h = tau[1] - tau[0]
+        sp = CubicSpline(tau, g, bc_type="not-a-knot")
+        d1, d2, d3 = sp.derivative(1), sp.derivative(2), sp.derivative(3)
+        iw = 1j * dmft.matsubara(beta, n_iw)
+        ref = (-(g[-1] + g[0]) / iw + (d1(tau[-1]) + d1(tau[0])) / iw ** 2 - (d2(tau[-1]) + d2(tau[0])) / iw ** 3
+               - (np.exp(iw * h) - 1.0) / iw ** 4 * (np.exp(np.outer(iw, tau[:-1])) @ d3(tau[:-1] + 0.5 * h)))
+        got = dmft.spline_ft(beta, tau, g, n_iw)
+        # rounding of either way of summing: a few N eps of sum |s3|, times the
+        # factor |(e^{iw h} - 1) / (iw)^4| (large at the lowest frequencies)
+        s3 = d3(tau[:-1] + 0.5 * h)
+        tol = 8 * N * np.finfo(float).eps * np.sum(np.abs(s3)) * np.abs((np.exp(iw * h) - 1.0) / iw ** 4) + 1e-14
+        assert np.all(np.abs(got - ref) <= tol)
+
+
 def test_ft_matches_oracle_quadrature():
     from oracle import dmft as od
     beta = 10.0
