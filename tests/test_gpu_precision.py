@@ -201,3 +201,14 @@ def test_paired_G_tau_on_a_self_consistent_insulating_bath():
     r, = paired_run(beta, [(U, beta / 200)], 32, 17, 20, 300, g0=[g0], n_wrap=64)
     assert r["stats"]["n_wrap"] == 64
     _assert_within(r, 50)
+
+
+def test_paired_G_tau_L500_large_grid_at_nwrap64():
+    """The large-Lambda configuration's grid (Lambda = 500, U = 4.8, beta = 50)
+    as it runs there: k = 64 requested (24 fits the G_up-only sweep's panels),
+    the refinement every 64 accepted flips; 16 chains, 30 sweeps, about 120
+    recomputes per chain."""
+    r, = paired_run(50.0, [(4.8, 0.1)], 16, 21, 4, 26, k=64, n_wrap=64)
+    assert r["stats"]["k"] == 24 and r["stats"]["n_wrap"] == 64 and r["stats"]["ph_symmetric"] == 1
+    assert r["stats"]["recompute_fallbacks"] == 0
+    _assert_within(r, 80)
