@@ -49,29 +49,37 @@ def extrapolate(dtaus, G_fine, err_fine=None):
     dtaus: n grids; G_fine: n x m values on the fine grid; err_fine: n x m
     error bars (None: equal weights).  Returns (a, sigma_a, b); sigma_a is
     propagated from the error bars through the fit, (X^T W X)^{-1}, which
-    stays defined when the fit has no residual degrees of freedom."""
+    stays defined when the fit has no residual degrees of freedom (NaN when
+    no error bars are given).  All points are solved at once: a QR
+    factorisation of the weighted design matrix per point, stacked."""
     x = np.asarray(dtaus, dtype=np.float64) ** 2
     G_fine = np.asarray(G_fine, dtype=np.float64)
     n, m = G_fine.shape
     # a + b x + c x^2 for three or more grids, a + b x for two; one grid is
     # the conventional fixed-dtau estimate itself (no extrapolation)
     deg = 2 if n >= 3 else (1 if n == 2 else 0)
-    a = np.empty(m)
+    X = np.vander(x, deg + 1)  # x^deg ... x^0
+    if err_fine is None:
+        w = np.ones((n, m))
+    else:
+        e = np.asarray(err_fine, dtype=np.float64)
+        pos = e > 0
+        # a non-positive error bar takes the smallest positive one of its point
+        floor = np.where(pos, e, np.inf).min(axis=0)
+        floor = np.where(np.isfinite(floor), floor, 1.0)
+        w = 1.0 / np.where(pos, e, floor[None, :])
+    Xw = X[None, :, :] * w.T[:, :, None]          # m x n x (deg+1)
+    yw = (G_fine * w).T[:, :, None]               # m x n x 1
+    Q, R = np.linalg.qr(Xw)                       # R: m x (deg+1) x (deg+1)
+    coef = np.linalg.solve(R, np.swapaxes(Q, 1, 2) @ yw)[:, :, 0]
+    a = coef[:, -1].copy()
+    b = coef[:, -2].copy() if deg > 0 else np.zeros(m)
     sa = np.full(m, np.nan)
-    b = np.empty(m)
-    X = np.vander(x, deg + 1)  # x^deg ... x^0, numpy's polyfit order
-    for t in range(m):
-        w = None
-        if err_fine is not None:
-            e = np.asarray(err_fine)[:, t]
-            w = 1.0 / np.where(e > 0, e, np.min(e[e > 0]) if np.any(e > 0) else 1.0)
-        coef = np.polyfit(x, G_fine[:, t], deg, w=w)
-        a[t] = coef[-1]
-        b[t] = coef[-2] if deg > 0 else 0.0
-        if w is not None:
-            Xw = X * w[:, None]
-            cov = np.linalg.inv(Xw.T @ Xw)
-            sa[t] = np.sqrt(cov[-1, -1])
+    if err_fine is not None:
+        # (X^T W X)^{-1} = R^{-1} R^{-T}: its last diagonal entry is the squared
+        # norm of the last row of R^{-1}
+        Rinv = np.linalg.inv(R)
+        sa = np.sqrt(np.sum(Rinv[:, -1, :] ** 2, axis=1))
     return a, sa, b
 
 

@@ -104,3 +104,38 @@ def test_gpu_multigrid_pipeline_matches_enumeration(orc):
     exact = [_exact_grid_G(orc, beta, U, L) for L in Ls]
     a_ex, _, _ = mg.multigrid_estimate(beta, dts, exact, list(Es), tf, ref)
     assert np.all(np.abs(a - a_ex)[1:-1] <= 4 * sa[1:-1] + 1e-6), np.max(np.abs(a - a_ex) / sa)
+
+
+def test_extrapolation_coefficients_and_error_propagation():
+    """The per-point weighted fit, solved for all fine points at once: with as
+    many grids as coefficients it interpolates, so a(tau) is the Lagrange
+    value at dtau = 0 and sigma_a^2 = sum_i (l_i(0) e_i)^2 with the Lagrange
+    basis l_i in x = dtau^2; with more grids a, b and sigma_a equal numpy's
+    weighted polyfit and its unscaled covariance, point by point; error
+    bars <= 0 take the smallest positive one of their point."""
+    rng = np.random.default_rng(11)
+    m = 7
+    for dts in ([0.5, 0.4], [0.5, 0.4, 0.25]):
+        x = np.asarray(dts) ** 2
+        n = len(dts)
+        G = rng.standard_normal((n, m))
+        E = rng.uniform(1e-4, 1e-3, (n, m))
+        a, sa, b = mg.extrapolate(dts, G, E)
+        ell0 = [np.prod([(0.0 - x[j]) / (x[i] - x[j]) for j in range(n) if j != i]) for i in range(n)]
+        np.testing.assert_allclose(a, sum(ell0[i] * G[i] for i in range(n)), rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(sa, np.sqrt(sum((ell0[i] * E[i]) ** 2 for i in range(n))), rtol=1e-9)
+    dts = [0.5, 0.4, 0.3, 0.25, 0.2, 1 / 6]
+    x = np.asarray(dts) ** 2
+    G = rng.standard_normal((6, m))
+    E = rng.uniform(1e-4, 1e-3, (6, m))
+    E[2, 3] = 0.0
+    a, sa, b = mg.extrapolate(dts, G, E)
+    for t in range(m):
+        e = E[:, t].copy()
+        e[e <= 0] = e[e > 0].min()
+        coef, cov = np.polyfit(x, G[:, t], 2, w=1.0 / e, cov="unscaled")
+        assert abs(a[t] - coef[-1]) < 1e-10 and abs(b[t] - coef[-2]) < 1e-8
+        assert abs(sa[t] - np.sqrt(cov[-1, -1])) < 1e-10 * max(1.0, sa[t])
+    a1, sa1, b1 = mg.extrapolate(dts, G, None)
+    assert np.all(np.isnan(sa1))
+    np.testing.assert_allclose(a1, [np.polyfit(x, G[:, t], 2)[-1] for t in range(m)], atol=1e-10)
