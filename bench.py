@@ -416,6 +416,9 @@ def run_ours(args, rank, world, local):
                        "grids_L": [g[2] for g in grids], "chains": [g[3] for g in grids],
                        "sweeps_per_step": S, "precision": args.precision,
                        "k": [st["k"] for st in stats], "n_wrap": [st["n_wrap"] for st in stats],
+                       # the delay depth asked for (0: the per-Lambda table); the library
+                       # lowers it to what fits in shared memory, "k" is the one used
+                       "k_requested": args.k,
                        "l2": "flushed (512 MiB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * args.steps,
